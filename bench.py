@@ -1,0 +1,497 @@
+"""Benchmark of the pre-packed tall-and-skinny GEMM on GB300.
+
+Workload (default, FP32): the memory-bound sweep  m = k = 32768,
+n in {1,2,4,8,16,32,64}, beta in {0,1}, alpha = 1, A and C0 uniform[-1,1] from
+the shared seeded generator, B packed once per n (packing untimed, as in the
+paper's evaluation, Section V).  One step = one tsmm_execute per (n, beta)
+point, 14 launches over a resident 4 GiB A (larger than L2, so no flush is
+needed between calls).  `--dtype f64` runs the same sweep in FP64.
+`--workload rankk` runs m = n = 16384, k in {4,...,128}, beta = 1.
+
+Metric: GFLOP/s by Eq. 7 (2*m*n*k / t) aggregated over the step, with the
+roofline of the dominant kernel; the CPU oracle on the host cores is timed on
+a bounded sample of the same workload as a baseline.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--dtype f32|f64]
+                  [--workload tall|rankk] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank runs the full workload on its own GPU
+(independent problems, weak scaling, no collective on the data path); rank 0
+prints the JSON line with value = all ranks' flops / max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "TSMM GFLOP/s & % HBM/FP roofline vs plain kernel; serving p50/p99 latency"
+UNIT = "GFLOP/s"
+SMS = 152
+FP32_LANES_PER_SM = 128
+SM_MAX_MHZ = 2070.0
+FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64 (non-tensor) nominal rate
+
+SWEEP_N = [1, 2, 4, 8, 16, 32, 64]
+SWEEP_BETA = [0.0, 1.0]
+RANKK_K = [4, 8, 16, 32, 64, 128]
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--dtype", choices=["f32", "f64"], default="f32")
+    p.add_argument("--workload", choices=["tall", "rankk"], default="tall")
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    return p.parse_args()
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def workload_points(args):
+    """(m, n, k, beta) per launch of one step."""
+    if args.workload == "tall":
+        return [(32768, n, 32768, b) for n in SWEEP_N for b in SWEEP_BETA]
+    return [(16384, 16384, k, 1.0) for k in RANKK_K]
+
+
+def workload_name(args):
+    if args.workload == "tall":
+        return (f"memory-bound sweep {args.dtype.upper()} m=k=32768, n in {SWEEP_N}, "
+                f"beta in {{0,1}}, alpha=1, B pre-packed and reused")
+    return f"rank-k {args.dtype.upper()} m=n=16384, k in {RANKK_K}, beta=1, B pre-packed"
+
+
+def alg_bytes(m, n, k, beta, es):
+    """Algorithmic bytes: A and B read once, C written once, C0 read if beta != 0."""
+    return es * (m * k + k * n + m * n * (1 + (1 if beta != 0 else 0)))
+
+
+def flops(m, n, k):
+    return 2.0 * m * n * k
+
+
+# --------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(prefix="clocks", suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        smax = [num(r[2]) for r in rows if num(r[2]) is not None]
+        pw = [num(r[3]) for r in rows if num(r[3]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        # median under load: samples within 30% of the top observed clock
+        top = max(sm) if sm else 0
+        loaded = [x for x in sm if x >= 0.3 * top] or sm
+        return {"sm_mhz": statistics.median(loaded) if loaded else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(pw) if pw else None,
+                "samples": len(rows), "reasons": reasons}
+
+
+# --------------------------------------------------------------------- oracle leg
+def oracle_sample(args, A_dev, budget_s=10.0):
+    """Time the CPU oracle, as it stands, on a bounded sample of the workload:
+    the first m_s rows of every point (same n, k, beta), with m_s sized from a
+    short calibration run so the sample takes about `budget_s` seconds.  The
+    rows of A are copied from the resident device A (same seeded generator)."""
+    import torch
+
+    import oracle
+    import tsmm_inputs as ti
+
+    npdt = np.float32 if args.dtype == "f32" else np.float64
+    pts = workload_points(args)
+    cores = oracle.num_threads()
+
+    def rows_of(m, k, m_s):
+        a = A_dev[(m, k)][:m_s]  # column-major m_s x k view
+        return np.asfortranarray(a.t().contiguous().cpu().numpy().T)
+
+    m0, n0, k0, _ = max(pts, key=lambda p: p[1] * p[2])
+    m_cal = min(m0, 512 * max(1, min(cores, 16)))
+    Acal = rows_of(m0, k0, m_cal)
+    Bcal = ti.matrix_np(k0, n0, ti.SEED_B, "uniform", npdt)
+    t0 = time.perf_counter()
+    oracle.tsmm(1.0, Acal, Bcal, 0.0, None)
+    rate = flops(m_cal, n0, k0) / max(time.perf_counter() - t0, 1e-4)
+    per_row = sum(flops(1, n, k) for (_, n, k, _) in pts)
+    m_s = int(budget_s * rate / per_row) // 256 * 256
+    m_s = max(256, min(m0, 8192, m_s))
+    sample = {}
+    for (m, n, k, beta) in pts:
+        if (m, k) not in sample:
+            sample[(m, k)] = rows_of(m, k, m_s)
+    Bs = {(n, k): ti.matrix_np(k, n, ti.SEED_B, "uniform", npdt) for (_, n, k, _) in pts}
+    C0s = {(m, n): np.asfortranarray(ti.rows_np(np.arange(m_s), m, n, ti.SEED_C0, "uniform", npdt))
+           for (m, n, _, _) in pts}
+    t0 = time.perf_counter()
+    fl = 0.0
+    for (m, n, k, beta) in pts:
+        oracle.tsmm(1.0, sample[(m, k)], Bs[(n, k)], beta, C0s[(m, n)] if beta != 0 else None)
+        fl += flops(m_s, n, k)
+    t = time.perf_counter() - t0
+    del torch
+    return {"value": round(fl / t / 1e9, 3), "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"first {m_s} rows of each of the {len(pts)} points of the workload "
+                      f"({fl / 1e9:.1f} GFLOP in {t:.1f} s)"}
+
+
+# --------------------------------------------------------------------- reference arm
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0  # rank 0 alone runs the CPU oracle
+    import oracle
+    import tsmm_inputs as ti
+
+    oracle.build()
+    npdt = np.float32 if args.dtype == "f32" else np.float64
+    pts = workload_points(args)
+    cores = oracle.num_threads()
+    kmax = max(k for (_, _, k, _) in pts)
+    # one step = the first m_s rows of every point; m_s sized for ~4 s per step
+    m_s = 256 * max(1, min(cores, 16)) // (2 if args.dtype == "f64" else 1)
+    m_s = min(m_s, pts[0][0])
+    A = ti.matrix_np(m_s, kmax, ti.SEED_A, "uniform", npdt)
+    Bs = {(n, k): ti.matrix_np(k, n, ti.SEED_B, "uniform", npdt) for (_, n, k, _) in pts}
+    C0s = {n: ti.matrix_np(m_s, n, ti.SEED_C0, "uniform", npdt) for (_, n, _, _) in pts}
+
+    def step():
+        fl = 0.0
+        for (m, n, k, beta) in pts:
+            Ak = A if k == kmax else np.asfortranarray(A[:, :k])
+            oracle.tsmm(1.0, Ak, Bs[(n, k)], beta, C0s[n] if beta != 0 else None)
+            fl += flops(m_s, n, k)
+        return fl
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    fl = 0.0
+    for _ in range(args.steps):
+        fl += step()
+    t = time.perf_counter() - t0
+    value = fl / t / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
+        "config": {"workload": workload_name(args), "sample_rows": m_s},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"first {m_s} rows of every point of the workload per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# --------------------------------------------------------------------- our arm
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2208_08088_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(name.encode())
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel_key):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on
+    the current kernel sources; else None."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+    except Exception:
+        return None
+    ent = d.get(kernel_key)
+    if not ent or ent.get("source_hash") != kernel_source_hash():
+        return None
+    return ent.get("dram_bytes_per_launch")
+
+
+def run_ours(args):
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    import paper_2208_08088_gb300 as tsmm
+    import tsmm_inputs as ti
+
+    tdt = torch.float32 if args.dtype == "f32" else torch.float64
+    es = 4 if args.dtype == "f32" else 8
+    pts = workload_points(args)
+    stream = torch.cuda.current_stream()
+
+    def dmat(rows, cols, seed):
+        t = torch.empty((cols, rows), dtype=tdt, device="cuda")
+        ti.fill_torch(t, seed, "uniform")
+        return t.t()
+
+    # resident inputs: one A per distinct k, one packed B + plan + C0 per point
+    A = {}
+    for (m, n, k, beta) in pts:
+        if (m, k) not in A:
+            A[(m, k)] = dmat(m, k, ti.SEED_A)
+    packed, plans, C = {}, {}, {}
+    for (m, n, k, beta) in pts:
+        if (n, k) not in packed:
+            packed[(n, k)] = tsmm.pack_b(dmat(k, n, ti.SEED_B))
+            plans[(m, n, k)] = tsmm.plan(m, n, k, tdt)
+            C[(m, n)] = dmat(m, n, ti.SEED_C0)  # C0; beta = 1 updates it in place
+    torch.cuda.synchronize()
+
+    def one(pt):
+        m, n, k, beta = pt
+        tsmm.execute(plans[(m, n, k)], 1.0, A[(m, k)], packed[(n, k)], beta, C[(m, n)])
+
+    # warm-up
+    for _ in range(args.warmup):
+        for pt in pts:
+            one(pt)
+    torch.cuda.synchronize()
+    for pl in plans.values():
+        pl.check()
+
+    ev = {pt: [] for pt in pts}
+    sampler = ClockSampler(local)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.3)
+    start = torch.cuda.Event(enable_timing=True)
+    stop = torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    for _ in range(args.steps):
+        for pt in pts:
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            one(pt)
+            e1.record(stream)
+            ev[pt].append((e0, e1))
+    stop.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = sampler.stop()
+    elapsed_ms = start.elapsed_time(stop)
+    for pl in plans.values():
+        pl.check()
+    if world > 1:
+        t = torch.tensor([elapsed_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+
+    step_flops = sum(flops(m, n, k) for (m, n, k, _) in pts)
+    value = world * step_flops * args.steps / (elapsed_ms * 1e-3) / 1e9
+    launches = args.steps * sum(plans[(m, n, k)].launches_per_execute() for (m, n, k, _) in pts)
+
+    hbm_peak, hbm_src = load_peaks()
+    fp32_peak_tf = SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    fp_peak_tf = fp32_peak_tf if args.dtype == "f32" else FP64_NOMINAL_TFLOPS
+
+    points = []
+    for pt in pts:
+        m, n, k, beta = pt
+        durs = [a.elapsed_time(b) for (a, b) in ev[pt]]
+        avg_ms = sum(durs) / len(durs)
+        gb = alg_bytes(m, n, k, beta, es) / 1e9
+        gbs = gb / (avg_ms * 1e-3)
+        tf = flops(m, n, k) / (avg_ms * 1e-3) / 1e12
+        # which roof binds: time at the HBM roof vs time at the FP roof
+        t_hbm = gb / hbm_peak
+        t_fp = flops(m, n, k) / (fp_peak_tf * 1e12)
+        bound = "hbm" if t_hbm >= t_fp else "alu"
+        frac = (gbs / hbm_peak) if bound == "hbm" else (tf / fp_peak_tf)
+        points.append({"m": m, "n": n, "k": k, "beta": beta, "avg_ms": round(avg_ms, 4),
+                       "gflops": round(tf * 1e3, 1), "alg_gbs": round(gbs, 1),
+                       "bound": bound, "frac": round(frac, 4), "total_ms": sum(durs)})
+    dom = max(points, key=lambda p: p["total_ms"])
+    m, n, k, beta = dom["m"], dom["n"], dom["k"], dom["beta"]
+    kernel_key = f"{args.workload}_{args.dtype}_n{n}_k{k}"
+    if dom["bound"] == "hbm":
+        roof = {"bound": "hbm", "achieved": dom["alg_gbs"], "peak": hbm_peak, "unit": "GB/s",
+                "frac": round(dom["alg_gbs"] / hbm_peak, 4),
+                "peak_source": f"{hbm_src} (MEASURED_PEAKS.json hbm_gbs)"}
+    else:
+        ach = dom["gflops"] / 1e3
+        roof = {"bound": "alu", "achieved": round(ach, 2), "peak": round(fp_peak_tf, 2),
+                "unit": "TFLOP/s", "frac": round(ach / fp_peak_tf, 4),
+                "peak_source": ("derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"
+                                if args.dtype == "f32" else "nominal GB300 FP64 rate 1.25 TFLOP/s")}
+    traffic = recorded_traffic(kernel_key)
+    roof["traffic"] = traffic
+    roof["kernel"] = f"{'tall' if args.workload == 'tall' else 'rankk'} {args.dtype} m={m} n={n} k={k} beta={beta}"
+    roof["alg_bytes_per_launch"] = alg_bytes(m, n, k, beta, es)
+    for p in points:
+        del p["total_ms"]
+
+    # ---------------- end to end: host buffers, copies inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(args, tsmm, torch, tdt, es, pts, A, packed, plans, world)
+
+    line = {
+        "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(elapsed_ms / args.steps, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
+        "config": {"workload": workload_name(args), "launches_per_step": len(pts),
+                   "alpha": 1.0, "l2": "no flush: each launch streams a >= 1 GiB operand, "
+                                         "larger than the 129 MB L2",
+                   "parallelism": f"replicas x{world} (independent problems per GPU)"},
+        "clocks": clocks, "gpu_launches": launches, "e2e": e2e, "roofline": roof,
+        "points": points,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu:
+        line["cpu_baseline"] = oracle_sample(args, A)
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def run_e2e(args, tsmm, torch, tdt, es, pts, A, packed, plans, world):
+    """Same metric through the public API with HOST buffers: each step copies
+    A (once, shared by every point) and the C0 of each beta != 0 point from
+    pinned host memory, executes, and reads every C back."""
+    stream = torch.cuda.current_stream()
+    hostA = {key: torch.empty_strided(a.shape, a.stride(), dtype=tdt, pin_memory=True)
+             for key, a in A.items()}
+    for key, h in hostA.items():
+        h.copy_(A[key])
+    hostC = {}
+    devA = {key: torch.empty_strided(h.shape, h.stride(), dtype=tdt, device="cuda")
+            for key, h in hostA.items()}
+    devC = {}
+    for (m, n, k, beta) in pts:
+        if (m, n) not in hostC:
+            hostC[(m, n)] = torch.empty_strided((m, n), (1, m), dtype=tdt, pin_memory=True)
+            hostC[(m, n)].fill_(0.5)
+            devC[(m, n)] = torch.empty_strided((m, n), (1, m), dtype=tdt, device="cuda")
+    h2d = d2h = 0
+    for key, h in hostA.items():
+        h2d += h.numel() * es
+    for (m, n, k, beta) in pts:
+        if beta != 0:
+            h2d += m * n * es
+        d2h += m * n * es
+    steps = max(2, args.steps // 4)
+
+    def step():
+        for key in hostA:
+            devA[key].copy_(hostA[key], non_blocking=True)
+        for (m, n, k, beta) in pts:
+            if beta != 0:
+                devC[(m, n)].copy_(hostC[(m, n)], non_blocking=True)
+            tsmm.execute(plans[(m, n, k)], 1.0, devA[(m, k)], packed[(n, k)], beta, devC[(m, n)])
+            hostC[(m, n)].copy_(devC[(m, n)], non_blocking=True)
+
+    step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(steps):
+        step()
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    fl = sum(flops(m, n, k) for (m, n, k, _) in pts)
+    del hostA, devA
+    return {"value": round(world * fl * steps / (ms * 1e-3) / 1e9, 1), "unit": UNIT,
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": steps,
+            "ms_per_step": round(ms / steps, 3)}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

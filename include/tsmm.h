@@ -1,0 +1,187 @@
+/*
+ * tsmm.h -- C ABI of the GB300 (sm_103a) pre-packed tall-and-skinny GEMM.
+ *
+ * The operation is Eq. 1 of "AutoTSMM: An Auto-tuning Framework for Building
+ * High-Performance Tall-and-Skinny Matrix-Matrix Multiplication on CPUs"
+ * (Li et al., arXiv 2208.08088):
+ *
+ *       C = alpha * A * B + beta * C0            A: m x k,  B: k x n,  C: m x n
+ *
+ * split, as the paper's Algorithm 1 ("Workflow of the pre-pack TSMM") splits
+ * it, into a packing step that runs once per B (PACKB, called there with
+ * alpha = 1) and a compute step that is executed many times against the
+ * packed operand (COMPUTE); the plan object is the GPU counterpart of the
+ * paper's runtime "execution plan" (Section III) that is generated once per
+ * problem shape and reused.
+ *
+ * Two shape regimes are supported (TSMM as defined in Section I: one operand
+ * has a dimension far smaller than the others):
+ *   regime (i)  n <= 64           (A tall: m and k large)   -- streaming kernel
+ *   regime (ii) n > 64, k <= 128  (rank-k update: m, n large) -- output-bound kernel
+ * Any other shape returns TSMM_ERR_UNSUPPORTED_SHAPE.
+ *
+ * Conventions shared by every entry point
+ *   - All matrices are column-major with explicit leading dimensions
+ *     (lda >= max(1,m), ldb >= max(1,k), ldc >= max(1,m)).
+ *   - Pointers named *_dev are device pointers on the current CUDA device.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     Every entry point that takes a stream only enqueues work on it and
+ *     returns without waiting; the returned status covers argument checks and
+ *     launch errors, not the outcome of the asynchronous work.
+ *   - alpha and beta are passed as double; for TSMM_F32 they are rounded to
+ *     float first.  alpha is applied once, in the epilogue (Eq. 1), never folded
+ *     into the packed B, so one packed B serves every alpha.
+ *   - BLAS conventions for the special cases: beta == 0 means C0 is not read
+ *     (C may hold NaN); alpha == 0 or k == 0 means A and B are not read and
+ *     C = beta*C0; m == 0 or n == 0 is a no-op returning TSMM_OK.
+ *   - Results are deterministic: split-K partial sums are combined in a fixed
+ *     order, so the same inputs give the same bits on every call.
+ *   - Out-parameters are written only when the call returns TSMM_OK.  No call
+ *     aborts or throws; every failure is a status code.
+ *   - Accuracy: every entry satisfies |C - C_exact| <= 4*k*u*(|alpha| sum_p
+ *     |A[i,p]||B[p,j]| + |beta||C0[i,j]|) with u = 2^-24 (F32) / 2^-53 (F64);
+ *     products are accumulated with IEEE fma in the working precision (no
+ *     TF32, no reduced-precision tensor-core path).
+ */
+#ifndef TSMM_H
+#define TSMM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define TSMM_API __attribute__((visibility("default")))
+#else
+#define TSMM_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum { TSMM_F32 = 0, TSMM_F64 = 1 } tsmm_dtype;
+
+typedef enum {
+    TSMM_OK = 0,
+    TSMM_ERR_INVALID_ARG = 1,      /* bad size, leading dimension, NULL pointer or dtype */
+    TSMM_ERR_UNSUPPORTED_SHAPE = 2,/* neither n <= 64 nor k <= 128 */
+    TSMM_ERR_MISMATCH = 3,         /* plan and packed B disagree on (k, n, dtype) or device */
+    TSMM_ERR_MISALIGNED = 4,       /* pointer not aligned to the element size */
+    TSMM_ERR_OUT_OF_MEMORY = 5,    /* device allocation failed */
+    TSMM_ERR_CUDA = 6,             /* a CUDA runtime/driver call failed */
+    TSMM_ERR_TIMEOUT = 7           /* a bounded device-side wait gave up (see tsmm_plan_check) */
+} tsmm_status;
+
+typedef void *tsmm_stream_t; /* a cudaStream_t */
+typedef struct tsmm_packed_b_s *tsmm_packed_b;
+typedef struct tsmm_plan_s *tsmm_plan_t;
+
+/* Human-readable name of a status code (static string, never NULL). */
+TSMM_API const char *tsmm_status_string(tsmm_status status);
+
+/* Library version as major*10000 + minor*100 + patch. */
+TSMM_API int tsmm_version(void);
+
+/*
+ * tsmm_pack_b -- PACKB of Algorithm 1: copy B (k x n, column-major, leading
+ * dimension ldb, device memory) into a library-owned, device-resident panel
+ * layout that the compute kernels read with contiguous accesses (the pre-pack
+ * module of Section IV.A.3).  The copy is bit-preserving and unscaled.
+ *
+ * Allocates the packed storage on the current device, enqueues one pack kernel
+ * on `stream` and returns the handle in *out.  The caller keeps ownership of
+ * B_dev and may free it once `stream` has passed the pack.  The handle owns its
+ * storage until tsmm_packed_b_destroy.  k == 0 or n == 0 is allowed (an empty
+ * handle).  Errors: INVALID_ARG (negative sizes, ldb < max(1,k), NULL out, or
+ * NULL B_dev with k*n > 0), UNSUPPORTED_SHAPE, MISALIGNED (B_dev not aligned to
+ * the element size), OUT_OF_MEMORY, CUDA.
+ *
+ * Packed layout (private to the library, described for test readers): the
+ * n columns are cut into `ntiles` tiles of `w` columns (regime (i): one tile,
+ * w = the kernel's padded column count; regime (ii): w = 128).  Tile t is a
+ * row-major kp x w block (kp = k rounded up to the kernel's k granule) at
+ * element offset t*kp*w; element (p, jj) of tile t holds B[p, t*w + jj], and is
+ * +0.0 where p >= k or t*w + jj >= n.
+ */
+TSMM_API tsmm_status tsmm_pack_b(tsmm_dtype dtype, int64_t k, int64_t n, const void *B_dev, int64_t ldb,
+                        tsmm_stream_t stream, tsmm_packed_b *out);
+
+/* Release a packed B (waits for the device to be done with it).  NULL is a no-op. */
+TSMM_API tsmm_status tsmm_packed_b_destroy(tsmm_packed_b pb);
+
+/*
+ * Describe a packed B: its dtype, k, n, kp, w, ntiles (see tsmm_pack_b), the
+ * device pointer of its storage and the storage size in bytes.  Any output
+ * pointer may be NULL.  The storage stays owned by the handle.
+ */
+TSMM_API tsmm_status tsmm_packed_b_info(tsmm_packed_b pb, tsmm_dtype *dtype, int64_t *k, int64_t *n,
+                               int64_t *kp, int64_t *w, int64_t *ntiles, const void **data_dev,
+                               size_t *bytes);
+
+/*
+ * Copy the packed storage of `pb` (tsmm_packed_b_info's `bytes` bytes) into host
+ * memory at host_dst, synchronously (waits for the pack to finish).  For tests
+ * and inspection.  Errors: INVALID_ARG (NULL pb, NULL host_dst with a non-empty
+ * pack, or `bytes` smaller than the packed size), CUDA.
+ */
+TSMM_API tsmm_status tsmm_packed_b_read(tsmm_packed_b pb, void *host_dst, size_t bytes);
+
+/*
+ * tsmm_plan -- the runtime "execution plan" of Section III / IV.A: chooses the
+ * kernel (regime (i) or (ii)), its tile shape, and the split of the k
+ * dimension across thread blocks (the GPU analogue of the cache-blocked
+ * designer and multi-thread optimizer: blocks are split along m and k, never
+ * along n, Section IV.A.2), and allocates the split-K workspace and the
+ * per-tile arrival counters on the current device.
+ *
+ * The plan is immutable once created and owns its workspace, so two
+ * executions that may overlap on the device (different streams) need two
+ * plans.  Errors: INVALID_ARG (negative sizes, bad dtype, NULL out),
+ * UNSUPPORTED_SHAPE, OUT_OF_MEMORY, CUDA.
+ */
+TSMM_API tsmm_status tsmm_plan(int64_t m, int64_t n, int64_t k, tsmm_dtype dtype, tsmm_plan_t *out);
+
+/* Release a plan (waits for the device to be done with it).  NULL is a no-op. */
+TSMM_API tsmm_status tsmm_plan_destroy(tsmm_plan_t plan);
+
+/*
+ * Describe a plan: regime (1 or 2), padded column count np, rows per thread
+ * block bm, number of k splits, and the workspace size in bytes.  Any output
+ * pointer may be NULL.
+ */
+TSMM_API tsmm_status tsmm_plan_info(tsmm_plan_t plan, int *regime, int *np, int *bm, int *splits,
+                           size_t *workspace_bytes);
+
+/*
+ * tsmm_execute -- COMPUTE of Algorithm 1:  C = alpha * A * packedB + beta * C0,
+ * where C0 is the prior content of C (in place, as in Eq. 1).
+ *
+ * A_dev: m x k, column-major, leading dimension lda, device memory, read only.
+ * C_dev: m x n, column-major, leading dimension ldc, read (if beta != 0) and
+ * written.  A and C must not overlap.  `pb` must have been packed with the
+ * plan's (k, n, dtype) on the same device (else TSMM_ERR_MISMATCH).
+ *
+ * A 16-byte aligned A with lda*sizeof(element) a multiple of 16 takes the
+ * TMA-staged kernel; other alignments take a slower kernel with plain loads
+ * (pointers must still be aligned to the element size, else MISALIGNED).
+ * Enqueues one or two kernels on `stream` and returns.
+ */
+TSMM_API tsmm_status tsmm_execute(tsmm_plan_t plan, double alpha, const void *A_dev, int64_t lda,
+                         tsmm_packed_b pb, double beta, void *C_dev, int64_t ldc,
+                         tsmm_stream_t stream);
+
+/*
+ * Synchronize the device and report whether any kernel launched with this plan
+ * has recorded a device-side error since the previous check (a bounded wait
+ * that ran out of iterations reports TSMM_ERR_TIMEOUT); clears the record.
+ */
+TSMM_API tsmm_status tsmm_plan_check(tsmm_plan_t plan);
+
+/* Number of kernel launches `tsmm_execute` with this plan enqueues (for accounting). */
+TSMM_API int tsmm_plan_launches_per_execute(tsmm_plan_t plan);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TSMM_H */

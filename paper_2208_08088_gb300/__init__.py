@@ -1,0 +1,282 @@
+"""Python binding of ``libtsmm.so``: the GB300 pre-packed tall-and-skinny GEMM.
+
+C = alpha * A * B + beta * C0  (Eq. 1 of AutoTSMM, arXiv 2208.08088), with B
+packed once (PACKB of Algorithm 1) and reused by many executions (COMPUTE).
+
+Two layers, both argument marshalling only -- every step of the computation
+runs in the CUDA kernels of the shared library:
+
+* ``tsmm_*`` functions with the C ABI's names and arguments (raw device
+  pointers as ints, sizes, a stream handle), raising ``TsmmError`` on a
+  non-OK status;
+* ``pack_b`` / ``plan`` / ``execute`` conveniences taking torch CUDA tensors
+  that hold column-major matrices (stride(0) == 1) and using the current
+  torch stream.
+
+The library must have been built first (``python paper_2208_08088_gb300/build.py``
+or ``__graft_entry__.build()``); importing the binding without it raises
+``ImportError`` -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+__all__ = [
+    "TsmmError", "F32", "F64", "lib", "library_path",
+    "tsmm_status_string", "tsmm_version", "tsmm_pack_b", "tsmm_packed_b_destroy",
+    "tsmm_packed_b_info", "tsmm_packed_b_read", "tsmm_plan", "tsmm_plan_destroy", "tsmm_plan_info", "tsmm_execute",
+    "tsmm_plan_check", "tsmm_plan_launches_per_execute",
+    "PackedB", "Plan", "pack_b", "plan", "execute", "colmajor", "ld_of",
+]
+
+F32, F64 = 0, 1
+STATUS = {
+    0: "TSMM_OK", 1: "TSMM_ERR_INVALID_ARG", 2: "TSMM_ERR_UNSUPPORTED_SHAPE",
+    3: "TSMM_ERR_MISMATCH", 4: "TSMM_ERR_MISALIGNED", 5: "TSMM_ERR_OUT_OF_MEMORY",
+    6: "TSMM_ERR_CUDA", 7: "TSMM_ERR_TIMEOUT",
+}
+
+library_path = _build.LIB
+
+
+class TsmmError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {STATUS.get(status, status)}")
+
+
+def _load():
+    if not os.path.exists(library_path):
+        raise ImportError(
+            f"{library_path} is missing: build the CUDA library first "
+            "(python paper_2208_08088_gb300/build.py); there is no CPU fallback")
+    L = ctypes.CDLL(library_path)
+    i64, dbl, vp, ci = ctypes.c_int64, ctypes.c_double, ctypes.c_void_p, ctypes.c_int
+    sz = ctypes.c_size_t
+    L.tsmm_status_string.restype = ctypes.c_char_p
+    L.tsmm_status_string.argtypes = [ci]
+    L.tsmm_version.restype = ci
+    L.tsmm_version.argtypes = []
+    L.tsmm_pack_b.restype = ci
+    L.tsmm_pack_b.argtypes = [ci, i64, i64, vp, i64, vp, ctypes.POINTER(vp)]
+    L.tsmm_packed_b_destroy.restype = ci
+    L.tsmm_packed_b_destroy.argtypes = [vp]
+    L.tsmm_packed_b_info.restype = ci
+    L.tsmm_packed_b_info.argtypes = [vp, ctypes.POINTER(ci)] + [ctypes.POINTER(i64)] * 5 + [
+        ctypes.POINTER(vp), ctypes.POINTER(sz)]
+    L.tsmm_packed_b_read.restype = ci
+    L.tsmm_packed_b_read.argtypes = [vp, vp, sz]
+    L.tsmm_plan.restype = ci
+    L.tsmm_plan.argtypes = [i64, i64, i64, ci, ctypes.POINTER(vp)]
+    L.tsmm_plan_destroy.restype = ci
+    L.tsmm_plan_destroy.argtypes = [vp]
+    L.tsmm_plan_info.restype = ci
+    L.tsmm_plan_info.argtypes = [vp] + [ctypes.POINTER(ci)] * 4 + [ctypes.POINTER(sz)]
+    L.tsmm_execute.restype = ci
+    L.tsmm_execute.argtypes = [vp, dbl, vp, i64, vp, dbl, vp, i64, vp]
+    L.tsmm_plan_check.restype = ci
+    L.tsmm_plan_check.argtypes = [vp]
+    L.tsmm_plan_launches_per_execute.restype = ci
+    L.tsmm_plan_launches_per_execute.argtypes = [vp]
+    return L
+
+
+lib = _load()
+
+
+def _check(status: int, where: str):
+    if status != 0:
+        raise TsmmError(status, where)
+
+
+# ------------------------------------------------------------------ C ABI names
+def tsmm_status_string(status: int) -> str:
+    return lib.tsmm_status_string(int(status)).decode()
+
+
+def tsmm_version() -> int:
+    return int(lib.tsmm_version())
+
+
+def tsmm_pack_b(dtype: int, k: int, n: int, B_dev: int, ldb: int, stream: int = 0) -> int:
+    out = ctypes.c_void_p()
+    _check(lib.tsmm_pack_b(dtype, k, n, B_dev or None, ldb, stream or None, ctypes.byref(out)),
+           "tsmm_pack_b")
+    return out.value
+
+
+def tsmm_packed_b_destroy(pb: int) -> None:
+    _check(lib.tsmm_packed_b_destroy(pb), "tsmm_packed_b_destroy")
+
+
+def tsmm_packed_b_info(pb: int) -> dict:
+    dt = ctypes.c_int()
+    k, n, kp, w, nt = (ctypes.c_int64() for _ in range(5))
+    data = ctypes.c_void_p()
+    nbytes = ctypes.c_size_t()
+    _check(lib.tsmm_packed_b_info(pb, ctypes.byref(dt), ctypes.byref(k), ctypes.byref(n),
+                                  ctypes.byref(kp), ctypes.byref(w), ctypes.byref(nt),
+                                  ctypes.byref(data), ctypes.byref(nbytes)), "tsmm_packed_b_info")
+    return dict(dtype=dt.value, k=k.value, n=n.value, kp=kp.value, w=w.value, ntiles=nt.value,
+                data=data.value or 0, bytes=nbytes.value)
+
+
+def tsmm_packed_b_read(pb: int, host_dst: int, nbytes: int) -> None:
+    _check(lib.tsmm_packed_b_read(pb, host_dst or None, nbytes), "tsmm_packed_b_read")
+
+
+def tsmm_plan(m: int, n: int, k: int, dtype: int) -> int:
+    out = ctypes.c_void_p()
+    _check(lib.tsmm_plan(m, n, k, dtype, ctypes.byref(out)), "tsmm_plan")
+    return out.value
+
+
+def tsmm_plan_destroy(plan: int) -> None:
+    _check(lib.tsmm_plan_destroy(plan), "tsmm_plan_destroy")
+
+
+def tsmm_plan_info(plan: int) -> dict:
+    regime, np_, bm, splits = (ctypes.c_int() for _ in range(4))
+    ws = ctypes.c_size_t()
+    _check(lib.tsmm_plan_info(plan, ctypes.byref(regime), ctypes.byref(np_), ctypes.byref(bm),
+                              ctypes.byref(splits), ctypes.byref(ws)), "tsmm_plan_info")
+    return dict(regime=regime.value, np=np_.value, bm=bm.value, splits=splits.value,
+                workspace_bytes=ws.value)
+
+
+def tsmm_execute(plan: int, alpha: float, A_dev: int, lda: int, pb: int, beta: float, C_dev: int,
+                 ldc: int, stream: int = 0) -> None:
+    _check(lib.tsmm_execute(plan, float(alpha), A_dev or None, lda, pb, float(beta), C_dev or None,
+                            ldc, stream or None), "tsmm_execute")
+
+
+def tsmm_plan_check(plan: int) -> None:
+    _check(lib.tsmm_plan_check(plan), "tsmm_plan_check")
+
+
+def tsmm_plan_launches_per_execute(plan: int) -> int:
+    return int(lib.tsmm_plan_launches_per_execute(plan))
+
+
+# ------------------------------------------------------------------ torch layer
+def _torch():
+    import torch
+    return torch
+
+
+def _dtype_code(t) -> int:
+    torch = _torch()
+    if t == torch.float32:
+        return F32
+    if t == torch.float64:
+        return F64
+    raise TypeError(f"unsupported dtype {t}")
+
+
+def _stream_handle(stream=None) -> int:
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def colmajor(rows: int, cols: int, dtype, device="cuda", ld: int | None = None, fill=None):
+    """A rows x cols column-major tensor (stride(0) == 1, stride(1) == ld)."""
+    torch = _torch()
+    ld = max(1, rows) if ld is None else ld
+    base = torch.empty((max(cols, 1), ld), dtype=dtype, device=device)
+    if fill is not None:
+        base.fill_(fill)
+    return base.t()[:rows, :cols]
+
+
+def ld_of(t) -> int:
+    """Leading dimension of a column-major 2-D tensor."""
+    if t.dim() != 2:
+        raise ValueError("expected a 2-D tensor")
+    if t.shape[0] > 1 and t.stride(0) != 1:
+        raise ValueError("tensor is not column-major (stride(0) != 1)")
+    return int(t.stride(1)) if t.shape[1] > 1 else max(1, int(t.shape[0]))
+
+
+class PackedB:
+    """Owner of a packed B handle (tsmm_pack_b / tsmm_packed_b_destroy)."""
+
+    def __init__(self, handle: int, k: int, n: int, dtype: int):
+        self.handle, self.k, self.n, self.dtype = handle, k, n, dtype
+
+    def info(self) -> dict:
+        return tsmm_packed_b_info(self.handle)
+
+    def read(self):
+        """The packed storage as a flat numpy array (synchronous copy)."""
+        import numpy as np
+        inf = self.info()
+        out = np.empty(inf["bytes"] // (8 if self.dtype == F64 else 4),
+                       dtype=np.float64 if self.dtype == F64 else np.float32)
+        tsmm_packed_b_read(self.handle, out.ctypes.data, out.nbytes)
+        return out
+
+    def close(self):
+        if self.handle:
+            tsmm_packed_b_destroy(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Plan:
+    """Owner of a plan handle (tsmm_plan / tsmm_plan_destroy)."""
+
+    def __init__(self, handle: int, m: int, n: int, k: int, dtype: int):
+        self.handle, self.m, self.n, self.k, self.dtype = handle, m, n, k, dtype
+
+    def info(self) -> dict:
+        return tsmm_plan_info(self.handle)
+
+    def check(self):
+        tsmm_plan_check(self.handle)
+
+    def launches_per_execute(self) -> int:
+        return tsmm_plan_launches_per_execute(self.handle)
+
+    def close(self):
+        if self.handle:
+            tsmm_plan_destroy(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def pack_b(B, stream=None) -> PackedB:
+    """Pack a column-major k x n CUDA tensor (enqueued on the current stream)."""
+    k, n = B.shape
+    dt = _dtype_code(B.dtype)
+    h = tsmm_pack_b(dt, k, n, B.data_ptr() if B.numel() else 0, ld_of(B) if k else 1,
+                    _stream_handle(stream))
+    return PackedB(h, k, n, dt)
+
+
+def plan(m: int, n: int, k: int, dtype) -> Plan:
+    dt = dtype if isinstance(dtype, int) else _dtype_code(dtype)
+    return Plan(tsmm_plan(m, n, k, dt), m, n, k, dt)
+
+
+def execute(p: Plan, alpha: float, A, pb: PackedB, beta: float, C, stream=None) -> None:
+    """C = alpha * A @ B + beta * C in place (column-major CUDA tensors)."""
+    if A.shape != (p.m, p.k) or C.shape != (p.m, p.n):
+        raise ValueError(f"shape mismatch: plan {(p.m, p.n, p.k)}, A {tuple(A.shape)}, C {tuple(C.shape)}")
+    lda = ld_of(A) if p.m > 0 and p.k > 0 else max(1, p.m)
+    tsmm_execute(p.handle, alpha, A.data_ptr() if A.numel() else 0, lda, pb.handle, beta,
+                 C.data_ptr() if C.numel() else 0, ld_of(C) if p.n > 0 else max(1, p.m),
+                 _stream_handle(stream))

@@ -1,0 +1,366 @@
+// The C ABI (include/tsmm.h): argument checking, the planner, packed-B and
+// plan lifetimes, and kernel dispatch.  No entry point throws or aborts.
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <climits>
+#include <cstring>
+#include <mutex>
+#include <new>
+
+#include "tsmm_device.cuh"
+#include "tsmm_internal.h"
+
+using namespace tsmm;
+
+namespace {
+
+constexpr int kVersion = 100;  // 0.1.0
+
+// Resolved once: the driver's tensor-map encoder (no -lcuda link needed).
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+std::once_flag g_encode_once;
+
+PFN_cuTensorMapEncodeTiled_v12000 encoder() {
+    std::call_once(g_encode_once, [] {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                             cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    });
+    return g_encode;
+}
+
+bool valid_dtype(tsmm_dtype d) { return d == TSMM_F32 || d == TSMM_F64; }
+
+bool aligned(const void *p, size_t a) { return reinterpret_cast<uintptr_t>(p) % a == 0; }
+
+tsmm_status cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return TSMM_OK;
+    if (e == cudaErrorMemoryAllocation) return TSMM_ERR_OUT_OF_MEMORY;
+    return TSMM_ERR_CUDA;
+}
+
+int current_device() {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return -1;
+    return dev;
+}
+
+// Split-K choice for regime (i): minimise a wave-quantised time model
+//   T(S) = ceil(slabs*S / resident) * (ceil(kstages / S) + overhead)
+// where `resident` thread blocks run at once (2 per SM) and `overhead` is the
+// per-block fixed cost (pipeline fill, reduction, epilogue) in stage units.
+// Smallest S wins ties, which also keeps the workspace small.
+int choose_splits(int64_t slabs, int64_t kstages, int num_sms, int64_t max_splits) {
+    const int64_t resident = 2LL * num_sms;
+    const int64_t overhead = 4;
+    int64_t best_s = 1;
+    double best_t = -1.0;
+    const int64_t s_max = std::max<int64_t>(1, std::min<int64_t>(kstages, max_splits));
+    for (int64_t s = 1; s <= s_max; ++s) {
+        const int64_t waves = (slabs * s + resident - 1) / resident;
+        const int64_t per = (kstages + s - 1) / s + overhead;
+        const double t = (double)waves * (double)per;
+        if (best_t < 0 || t < best_t) {
+            best_t = t;
+            best_s = s;
+        }
+    }
+    return (int)best_s;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *tsmm_status_string(tsmm_status status) {
+    switch (status) {
+        case TSMM_OK: return "TSMM_OK";
+        case TSMM_ERR_INVALID_ARG: return "TSMM_ERR_INVALID_ARG";
+        case TSMM_ERR_UNSUPPORTED_SHAPE: return "TSMM_ERR_UNSUPPORTED_SHAPE";
+        case TSMM_ERR_MISMATCH: return "TSMM_ERR_MISMATCH";
+        case TSMM_ERR_MISALIGNED: return "TSMM_ERR_MISALIGNED";
+        case TSMM_ERR_OUT_OF_MEMORY: return "TSMM_ERR_OUT_OF_MEMORY";
+        case TSMM_ERR_CUDA: return "TSMM_ERR_CUDA";
+        case TSMM_ERR_TIMEOUT: return "TSMM_ERR_TIMEOUT";
+    }
+    return "TSMM_ERR_UNKNOWN";
+}
+
+int tsmm_version(void) { return kVersion; }
+
+tsmm_status tsmm_pack_b(tsmm_dtype dtype, int64_t k, int64_t n, const void *B_dev, int64_t ldb,
+                        tsmm_stream_t stream, tsmm_packed_b *out) {
+    if (!out || !valid_dtype(dtype) || k < 0 || n < 0) return TSMM_ERR_INVALID_ARG;
+    if (ldb < std::max<int64_t>(1, k)) return TSMM_ERR_INVALID_ARG;
+    if (k > 0 && n > 0 && !B_dev) return TSMM_ERR_INVALID_ARG;
+    const size_t es = dtype_size(dtype);
+    if (B_dev && !aligned(B_dev, es)) return TSMM_ERR_MISALIGNED;
+    const int regime = regime_of(k, n);
+    if (regime == 0) return TSMM_ERR_UNSUPPORTED_SHAPE;
+    const int dev = current_device();
+    if (dev < 0) return TSMM_ERR_CUDA;
+
+    tsmm_packed_b pb = new (std::nothrow) tsmm_packed_b_s();
+    if (!pb) return TSMM_ERR_OUT_OF_MEMORY;
+    pb->dtype = dtype;
+    pb->k = k;
+    pb->n = n;
+    pb->regime = regime;
+    pb->device = dev;
+    if (regime == 1) {
+        pb->kp = round_up(k, kTallBKS);
+        pb->w = tall_np(n);
+        pb->ntiles = 1;
+    } else {
+        pb->kp = round_up(k, kRankKGran);
+        pb->w = kRankNT;
+        pb->ntiles = (n + kRankNT - 1) / kRankNT;
+    }
+    pb->bytes = (size_t)(pb->kp * pb->w * pb->ntiles) * es;
+    pb->data = nullptr;
+    if (pb->bytes > 0) {
+        cudaError_t e = cudaMalloc(&pb->data, pb->bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            delete pb;
+            return cuda_status(e);
+        }
+        e = launch_pack_b(dtype, k, n, B_dev, ldb, pb->data, pb->kp, pb->w, pb->ntiles,
+                          static_cast<cudaStream_t>(stream));
+        if (e != cudaSuccess) {
+            cudaFree(pb->data);
+            delete pb;
+            return cuda_status(e);
+        }
+    }
+    *out = pb;
+    return TSMM_OK;
+}
+
+tsmm_status tsmm_packed_b_destroy(tsmm_packed_b pb) {
+    if (!pb) return TSMM_OK;
+    tsmm_status st = TSMM_OK;
+    if (pb->data) st = cuda_status(cudaFree(pb->data));
+    delete pb;
+    return st;
+}
+
+tsmm_status tsmm_packed_b_info(tsmm_packed_b pb, tsmm_dtype *dtype, int64_t *k, int64_t *n,
+                               int64_t *kp, int64_t *w, int64_t *ntiles, const void **data_dev,
+                               size_t *bytes) {
+    if (!pb) return TSMM_ERR_INVALID_ARG;
+    if (dtype) *dtype = pb->dtype;
+    if (k) *k = pb->k;
+    if (n) *n = pb->n;
+    if (kp) *kp = pb->kp;
+    if (w) *w = pb->w;
+    if (ntiles) *ntiles = pb->ntiles;
+    if (data_dev) *data_dev = pb->data;
+    if (bytes) *bytes = pb->bytes;
+    return TSMM_OK;
+}
+
+tsmm_status tsmm_packed_b_read(tsmm_packed_b pb, void *host_dst, size_t bytes) {
+    if (!pb || bytes < pb->bytes || (pb->bytes > 0 && !host_dst)) return TSMM_ERR_INVALID_ARG;
+    if (pb->bytes == 0) return TSMM_OK;
+    if (cudaDeviceSynchronize() != cudaSuccess) return TSMM_ERR_CUDA;
+    return cuda_status(cudaMemcpy(host_dst, pb->data, pb->bytes, cudaMemcpyDeviceToHost));
+}
+
+tsmm_status tsmm_plan(int64_t m, int64_t n, int64_t k, tsmm_dtype dtype, tsmm_plan_t *out) {
+    if (!out || !valid_dtype(dtype) || m < 0 || n < 0 || k < 0) return TSMM_ERR_INVALID_ARG;
+    const int regime = regime_of(k, n);
+    if (regime == 0) return TSMM_ERR_UNSUPPORTED_SHAPE;
+    const int dev = current_device();
+    if (dev < 0) return TSMM_ERR_CUDA;
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return TSMM_ERR_CUDA;
+
+    tsmm_plan_t p = new (std::nothrow) tsmm_plan_s();
+    if (!p) return TSMM_ERR_OUT_OF_MEMORY;
+    std::memset(static_cast<void *>(p), 0, sizeof(*p));
+    p->m = m;
+    p->n = n;
+    p->k = k;
+    p->dtype = dtype;
+    p->regime = regime;
+    p->device = dev;
+    p->num_sms = sms;
+    const size_t es = dtype_size(dtype);
+    size_t ticket_bytes = 0;
+    if (regime == 1) {
+        p->np = tall_np(n);
+        p->bm = tall_bm(dtype);
+        p->kp = round_up(k, kTallBKS);
+        p->slabs = (m + p->bm - 1) / p->bm;
+        const int64_t kstages = p->kp / kTallBKS;
+        // keep the workspace within 512 MiB and the grid's y extent legal
+        const int64_t per_split = (int64_t)p->np * p->slabs * p->bm * (int64_t)es;
+        int64_t max_splits = 65535;
+        if (per_split > 0) max_splits = std::min<int64_t>(max_splits, (512LL << 20) / per_split);
+        int s = (kstages > 0 && p->slabs > 0) ? choose_splits(p->slabs, kstages, sms, max_splits) : 1;
+        const int64_t chunk_stages = kstages > 0 ? (kstages + s - 1) / s : 1;
+        p->kchunk = chunk_stages * kTallBKS;
+        p->splits = kstages > 0 ? (int)((kstages + chunk_stages - 1) / chunk_stages) : 1;
+        if (p->splits > 1) {
+            p->workspace_bytes = (size_t)p->splits * (size_t)per_split;
+            ticket_bytes = (size_t)p->slabs * sizeof(unsigned);
+        }
+    } else {
+        p->kp = round_up(k, kRankKGran);
+        p->bm = dtype == TSMM_F64 ? 64 : 128;
+        p->np = kRankNT;
+        p->splits = 1;
+        p->mtiles = (m + p->bm - 1) / p->bm;
+        p->ntiles = (n + kRankNT - 1) / kRankNT;
+    }
+    cudaError_t e = cudaSuccess;
+    if (p->workspace_bytes) e = cudaMalloc(&p->workspace, p->workspace_bytes);
+    if (e == cudaSuccess && ticket_bytes) {
+        e = cudaMalloc(reinterpret_cast<void **>(&p->tickets), ticket_bytes);
+        if (e == cudaSuccess) e = cudaMemset(p->tickets, 0, ticket_bytes);
+    }
+    if (e == cudaSuccess) {
+        e = cudaMalloc(reinterpret_cast<void **>(&p->status), sizeof(unsigned));
+        if (e == cudaSuccess) e = cudaMemset(p->status, 0, sizeof(unsigned));
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        if (p->workspace) cudaFree(p->workspace);
+        if (p->tickets) cudaFree(p->tickets);
+        if (p->status) cudaFree(p->status);
+        delete p;
+        return cuda_status(e);
+    }
+    *out = p;
+    return TSMM_OK;
+}
+
+tsmm_status tsmm_plan_destroy(tsmm_plan_t p) {
+    if (!p) return TSMM_OK;
+    tsmm_status st = TSMM_OK;
+    if (p->workspace && cudaFree(p->workspace) != cudaSuccess) st = TSMM_ERR_CUDA;
+    if (p->tickets && cudaFree(p->tickets) != cudaSuccess) st = TSMM_ERR_CUDA;
+    if (p->status && cudaFree(p->status) != cudaSuccess) st = TSMM_ERR_CUDA;
+    delete p;
+    return st;
+}
+
+tsmm_status tsmm_plan_info(tsmm_plan_t p, int *regime, int *np, int *bm, int *splits,
+                           size_t *workspace_bytes) {
+    if (!p) return TSMM_ERR_INVALID_ARG;
+    if (regime) *regime = p->regime;
+    if (np) *np = p->np;
+    if (bm) *bm = p->bm;
+    if (splits) *splits = p->splits;
+    if (workspace_bytes) *workspace_bytes = p->workspace_bytes;
+    return TSMM_OK;
+}
+
+int tsmm_plan_launches_per_execute(tsmm_plan_t p) {
+    if (!p) return 0;
+    return (p->m == 0 || p->n == 0) ? 0 : 1;
+}
+
+tsmm_status tsmm_execute(tsmm_plan_t p, double alpha, const void *A_dev, int64_t lda,
+                         tsmm_packed_b pb, double beta, void *C_dev, int64_t ldc,
+                         tsmm_stream_t stream) {
+    if (!p || !pb) return TSMM_ERR_INVALID_ARG;
+    if (pb->dtype != p->dtype || pb->k != p->k || pb->n != p->n || pb->device != p->device)
+        return TSMM_ERR_MISMATCH;
+    if (current_device() != p->device) return TSMM_ERR_MISMATCH;
+    const int64_t m = p->m, n = p->n, k = p->k;
+    if (lda < std::max<int64_t>(1, m) || ldc < std::max<int64_t>(1, m)) return TSMM_ERR_INVALID_ARG;
+    if (m == 0 || n == 0) return TSMM_OK;
+    const bool use_ab = (alpha != 0.0) && (k > 0);
+    if (!C_dev || (use_ab && !A_dev)) return TSMM_ERR_INVALID_ARG;
+    const size_t es = dtype_size(p->dtype);
+    if (!aligned(C_dev, es) || (use_ab && !aligned(A_dev, es))) return TSMM_ERR_MISALIGNED;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (p->dtype == TSMM_F32 && static_cast<float>(alpha) == 0.0f && alpha != 0.0) {
+        // alpha underflows to zero in float: behave as alpha == 0
+        return cuda_status(launch_scale(p->dtype, m, n, beta, C_dev, ldc, s));
+    }
+    if (!use_ab) return cuda_status(launch_scale(p->dtype, m, n, beta, C_dev, ldc, s));
+
+    if (p->regime == 2) {
+        RankArgs a;
+        a.m = m;
+        a.n = n;
+        a.k = k;
+        a.lda = lda;
+        a.ldc = ldc;
+        a.kp = pb->kp;
+        a.A = A_dev;
+        a.Bp = pb->data;
+        a.C = C_dev;
+        a.alpha = alpha;
+        a.beta = beta;
+        return cuda_status(launch_rankk(p->dtype, a, s));
+    }
+
+    TallArgs a;
+    a.m = m;
+    a.n = n;
+    a.k = k;
+    a.lda = lda;
+    a.ldc = ldc;
+    a.A = A_dev;
+    a.Bp = pb->data;
+    a.C = C_dev;
+    a.alpha = alpha;
+    a.beta = beta;
+    a.ws = p->workspace;
+    a.tickets = p->tickets;
+    a.status = p->status;
+    a.splits = p->splits;
+    a.kchunk = p->kchunk;
+    a.kp = p->kp;
+    a.slabs = p->slabs;
+
+    const bool tma = aligned(A_dev, 16) && ((lda * (int64_t)es) % 16 == 0) && m < INT_MAX &&
+                     k < INT_MAX && (lda * (int64_t)es) < (1LL << 40) && encoder() != nullptr;
+    if (tma && (p->tmap_ptr != A_dev || p->tmap_lda != lda)) {
+        const cuuint64_t gdim[2] = {(cuuint64_t)m, (cuuint64_t)k};
+        const cuuint64_t gstride[1] = {(cuuint64_t)(lda * (int64_t)es)};
+        const cuuint32_t box[2] = {(cuuint32_t)p->bm, (cuuint32_t)kTallBKS};
+        const cuuint32_t estr[2] = {1, 1};
+        CUresult r = encoder()(&p->tmap,
+                               p->dtype == TSMM_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                                    : CU_TENSOR_MAP_DATA_TYPE_FLOAT64,
+                               2, const_cast<void *>(A_dev), gdim, gstride, box, estr,
+                               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                               CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) {
+            p->tmap_ptr = nullptr;
+            return TSMM_ERR_CUDA;
+        }
+        p->tmap_ptr = A_dev;
+        p->tmap_lda = lda;
+    }
+    cudaError_t e = p->dtype == TSMM_F32 ? launch_tall_f32(tma, p->np, &p->tmap, a, s)
+                                         : launch_tall_f64(tma, p->np, &p->tmap, a, s);
+    return cuda_status(e);
+}
+
+tsmm_status tsmm_plan_check(tsmm_plan_t p) {
+    if (!p) return TSMM_ERR_INVALID_ARG;
+    if (cudaDeviceSynchronize() != cudaSuccess) return TSMM_ERR_CUDA;
+    unsigned word = 0;
+    if (cudaMemcpy(&word, p->status, sizeof(word), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return TSMM_ERR_CUDA;
+    if (word == 0) return TSMM_OK;
+    // clear the record and the split-K arrival counters a failed launch may have left
+    cudaMemset(p->status, 0, sizeof(unsigned));
+    if (p->tickets) cudaMemset(p->tickets, 0, (size_t)p->slabs * sizeof(unsigned));
+    cudaDeviceSynchronize();
+    return (word & kDevErrTimeout) ? TSMM_ERR_TIMEOUT : TSMM_ERR_CUDA;
+}
+
+}  // extern "C"

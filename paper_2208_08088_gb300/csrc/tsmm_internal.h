@@ -1,0 +1,121 @@
+// Internal (host-side) declarations shared by the library's translation units.
+#pragma once
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+#include "../../include/tsmm.h"
+
+namespace tsmm {
+
+// ---- tiling constants shared by planner, packer and kernels -------------------
+// Regime (i): A columns per pipeline stage; packed B rows are padded to it.
+constexpr int kTallBKS = 32;
+// Regime (i): consumer warps per thread block (the producer warp is extra).
+constexpr int kTallConsumerWarps = 4;
+// Regime (ii): packed B tile width (columns) and k granule.
+constexpr int kRankNT = 128;
+constexpr int kRankKGran = 8;
+constexpr int kRankMaxK = 128;
+constexpr int kTallMaxN = 64;
+
+inline size_t dtype_size(tsmm_dtype d) { return d == TSMM_F64 ? 8 : 4; }
+
+// Padded column count of the regime-(i) kernel that serves n columns.
+inline int tall_np(int64_t n) {
+    int np = 1;
+    while (np < n) np <<= 1;
+    return np;
+}
+
+// Rows per thread block of the regime-(i) kernel (see tall kernel header).
+inline int tall_bm(tsmm_dtype d) { return d == TSMM_F64 ? 64 : 128; }
+
+// Regime of a (k, n) pair: 1 = tall (n <= 64), 2 = rank-k (k <= 128), 0 = unsupported.
+inline int regime_of(int64_t k, int64_t n) {
+    if (n <= kTallMaxN) return 1;
+    if (k <= kRankMaxK) return 2;
+    return 0;
+}
+
+inline int64_t round_up(int64_t x, int64_t g) { return (x + g - 1) / g * g; }
+
+}  // namespace tsmm
+
+struct tsmm_packed_b_s {
+    tsmm_dtype dtype;
+    int64_t k, n;
+    int64_t kp;      // padded rows
+    int64_t w;       // tile width (columns)
+    int64_t ntiles;  // number of column tiles
+    int regime;
+    int device;
+    void *data;      // device storage, kp * w * ntiles elements
+    size_t bytes;
+};
+
+struct tsmm_plan_s {
+    int64_t m, n, k;
+    tsmm_dtype dtype;
+    int regime;
+    int device;
+    int num_sms;
+    // regime (i)
+    int np;          // padded n
+    int bm;          // rows per thread block
+    int64_t slabs;   // ceil(m / bm)
+    int splits;      // k splits (S)
+    int64_t kchunk;  // packed-B rows per split (multiple of kTallBKS)
+    int64_t kp;      // padded k
+    // regime (ii)
+    int64_t mtiles, ntiles;
+    // device scratch owned by the plan
+    void *workspace;           // splits * np * slabs * bm elements (regime (i), splits > 1)
+    size_t workspace_bytes;
+    unsigned *tickets;         // one arrival counter per slab
+    unsigned *status;          // device error word
+    // one-entry cache of the TMA descriptor for A
+    const void *tmap_ptr;
+    int64_t tmap_lda;
+    CUtensorMap tmap;
+};
+
+namespace tsmm {
+
+struct TallArgs {
+    int64_t m, n, k, lda, ldc;
+    const void *A;
+    const void *Bp;     // packed B, kp x np row-major
+    void *C;
+    double alpha, beta;
+    void *ws;
+    unsigned *tickets;
+    unsigned *status;
+    int splits;
+    int64_t kchunk, kp, slabs;
+};
+
+// Launchers (return cudaSuccess or the launch error).  `tma` selects the
+// TMA-pipelined kernel (tmap must describe A) or the plain-load kernel.
+cudaError_t launch_tall_f32(bool tma, int np, const CUtensorMap *tmap, const TallArgs &a,
+                            cudaStream_t s);
+cudaError_t launch_tall_f64(bool tma, int np, const CUtensorMap *tmap, const TallArgs &a,
+                            cudaStream_t s);
+
+struct RankArgs {
+    int64_t m, n, k, lda, ldc, kp;
+    const void *A;
+    const void *Bp;  // packed B, ntiles x (kp x kRankNT)
+    void *C;
+    double alpha, beta;
+};
+cudaError_t launch_rankk(tsmm_dtype dt, const RankArgs &a, cudaStream_t s);
+
+cudaError_t launch_pack_b(tsmm_dtype dt, int64_t k, int64_t n, const void *B, int64_t ldb,
+                          void *dst, int64_t kp, int64_t w, int64_t ntiles, cudaStream_t s);
+cudaError_t launch_scale(tsmm_dtype dt, int64_t m, int64_t n, double beta, void *C, int64_t ldc,
+                         cudaStream_t s);
+
+}  // namespace tsmm

@@ -1,0 +1,386 @@
+// Regime (i) kernel: C[m x n] = alpha * A[m x k] * B[k x n] + beta * C0, n <= 64.
+//
+// Mapping of the paper's tiled algorithm (Section IV.A, Fig. 2) to the GPU:
+//   * GEPB_t (a block of m_t rows per CPU thread) -> a thread block owns an
+//     m-slab of BM rows and a contiguous k range.  n is never split across
+//     blocks (the paper leaves n untiled when n <= n_c, Section IV.A.2), so each
+//     block stages the full-width rows of packed B it needs in shared memory,
+//     the counterpart of each core keeping its B block in its own L1.
+//   * No barrier between k iterations thanks to pre-packing (Section IV.A.2)
+//     -> blocks never wait for each other: the k splits of a slab are combined
+//     by whichever block finishes last (an atomic arrival ticket; nobody
+//     spins), in the fixed order s = 0..S-1.
+//   * Register-blocked m_r x n_r inner kernels (Section IV.B) -> each thread
+//     keeps an R x CN register tile of C; A arrives through a multi-stage TMA
+//     pipeline (the GPU form of the paper's prefetching, Section IV.B.3), and B
+//     rows are read from shared memory as broadcasts.
+//
+// Block layout: kTallConsumerWarps consumer warps + 1 producer warp.  The
+// producer issues, per stage, one 2-D tensor copy of A (BM rows x BKS columns,
+// zero-filled outside the matrix) and one bulk copy of BKS packed B rows.
+// Consumer warps are arranged WM (along m) x WK (along k); lanes are arranged
+// LR (along m) x G (along n).  After the k loop the WK partial tiles are summed
+// in shared memory in warp order, then either stored (one split) or written to
+// the split-K workspace and finished by the last-arriving block.
+#pragma once
+#include "tsmm_device.cuh"
+#include "tsmm_internal.h"
+
+namespace tsmm {
+
+template <typename T, int NP>
+struct TallCfg {
+    static constexpr int VEC = 16 / (int)sizeof(T);   // elements per 16-byte vector
+    static constexpr int R = VEC;                      // rows per thread
+    static constexpr int CN = NP < 16 ? NP : 16;       // columns per thread
+    static constexpr int G = NP / CN;                  // lane groups along n
+    static constexpr int LR = 32 / G;                  // lanes along m
+    static constexpr int WROWS = LR * R;               // rows per warp
+    static constexpr int BM = (sizeof(T) == 4) ? 128 : 64;
+    static constexpr int WM = BM / WROWS;              // warps along m
+    static constexpr int NWARPS = kTallConsumerWarps;
+    static constexpr int WK = NWARPS / WM;             // warps along k
+    static constexpr int BKS = kTallBKS;
+    static constexpr int KPW = BKS / WK;               // stage columns per warp
+    static constexpr int BV = CN < VEC ? CN : VEC;     // B vector width
+    static constexpr int A_STAGE = BM * BKS;           // elements
+    static constexpr int B_STAGE = BKS * NP;           // elements
+    static constexpr int STAGE_BYTES = (A_STAGE + B_STAGE) * (int)sizeof(T);
+    static constexpr int STAGES_RAW = (100 * 1024) / STAGE_BYTES;
+    static constexpr int STAGES = STAGES_RAW < 2 ? 2 : (STAGES_RAW > 6 ? 6 : STAGES_RAW);
+    static constexpr int RED = WK * NP * BM;           // reduction buffer elements
+    static constexpr int DATA_BYTES = STAGES * STAGE_BYTES > RED * (int)sizeof(T)
+                                          ? STAGES * STAGE_BYTES
+                                          : RED * (int)sizeof(T);
+    static constexpr int SMEM = DATA_BYTES + 2 * STAGES * 8 + 16;
+    static constexpr int THREADS = (NWARPS + 1) * 32;
+    static constexpr int CONSUMERS = NWARPS * 32;
+    static_assert(G * CN == NP, "column split");
+    static_assert(WM * WROWS == BM && WM <= NWARPS && WK * WM == NWARPS, "warp split");
+    static_assert(WK * KPW == BKS, "stage split");
+    static_assert(BM * (int)sizeof(T) % 16 == 0, "TMA box row bytes");
+};
+
+// Sum of the WK per-warp partial tiles, then store / split-K finish.
+// `red` holds WK tiles laid out [WK][NP][BM]; on return red[0..NP*BM) is reused.
+template <typename T, int NP>
+__device__ __forceinline__ void tall_finish(T *red, const TallArgs &a, int64_t slab, int split,
+                                            int ctid, unsigned *smem_flag) {
+    using Cfg = TallCfg<T, NP>;
+    constexpr int R = Cfg::R;
+    constexpr int CHUNKS = NP * Cfg::BM / R;
+    const T alpha = static_cast<T>(a.alpha);
+    const T beta = static_cast<T>(a.beta);
+    const int64_t row0 = slab * Cfg::BM;
+
+    // 1) cross-warp sum in warp order w = 0..WK-1
+    if (Cfg::WK > 1) {
+        for (int q = ctid; q < CHUNKS; q += Cfg::CONSUMERS) {
+            Vec<T, R> s = ld_vec<T, R>(red + q * R);
+#pragma unroll
+            for (int w = 1; w < Cfg::WK; ++w) {
+                Vec<T, R> t = ld_vec<T, R>(red + w * NP * Cfg::BM + q * R);
+#pragma unroll
+                for (int r = 0; r < R; ++r) s.v[r] += t.v[r];
+            }
+            st_vec<T, R>(red + q * R, s);
+        }
+        named_barrier(1, Cfg::CONSUMERS);
+    }
+
+    auto store = [&](int q, const Vec<T, R> &v) {
+        const int j = (q * R) / Cfg::BM;
+        const int il = (q * R) % Cfg::BM;
+        if (j >= a.n) return;
+        T *cptr = static_cast<T *>(a.C);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int64_t i = row0 + il + r;
+            if (i < a.m) {
+                T out = alpha * v.v[r];
+                T *c = cptr + i + (int64_t)j * a.ldc;
+                if (beta != T(0)) out = fma(beta, *c, out);
+                *c = out;
+            }
+        }
+    };
+
+    if (a.splits == 1) {
+        for (int q = ctid; q < CHUNKS; q += Cfg::CONSUMERS) store(q, ld_vec<T, R>(red + q * R));
+        return;
+    }
+
+    // 2) split-K: publish this block's partial tile, take an arrival ticket
+    const int64_t mpad = a.slabs * Cfg::BM;
+    T *ws = static_cast<T *>(a.ws);
+    for (int q = ctid; q < CHUNKS; q += Cfg::CONSUMERS) {
+        const int j = (q * R) / Cfg::BM;
+        const int il = (q * R) % Cfg::BM;
+        st_vec<T, R>(ws + ((int64_t)split * NP + j) * mpad + row0 + il, ld_vec<T, R>(red + q * R));
+    }
+    __threadfence();
+    named_barrier(1, Cfg::CONSUMERS);
+    if (ctid == 0) {
+        const unsigned ticket = atomicAdd(a.tickets + slab, 1u);
+        *smem_flag = (ticket == (unsigned)(a.splits - 1)) ? 1u : 0u;
+    }
+    named_barrier(1, Cfg::CONSUMERS);
+    if (*smem_flag == 0u) return;
+
+    // 3) last arriver: sum the S partial tiles in the fixed order s = 0..S-1
+    __threadfence();
+    for (int q = ctid; q < CHUNKS; q += Cfg::CONSUMERS) {
+        const int j = (q * R) / Cfg::BM;
+        const int il = (q * R) % Cfg::BM;
+        Vec<T, R> s;
+#pragma unroll
+        for (int r = 0; r < R; ++r) s.v[r] = T(0);
+        for (int sp = 0; sp < a.splits; ++sp) {
+            Vec<T, R> t;
+            if (sp == split) {
+                t = ld_vec<T, R>(red + q * R);
+            } else {
+                const T *src = ws + ((int64_t)sp * NP + j) * mpad + row0 + il;
+#pragma unroll
+                for (int r = 0; r < R; ++r) t.v[r] = ld_cg(src + r);
+            }
+#pragma unroll
+            for (int r = 0; r < R; ++r) s.v[r] += t.v[r];
+        }
+        store(q, s);
+    }
+    if (ctid == 0) a.tickets[slab] = 0u;  // ready for the next launch on this stream
+}
+
+// Accumulate one A column (R rows, vector) against NP packed B values.
+template <typename T, int NP>
+__device__ __forceinline__ void tall_fma_column(T (&acc)[TallCfg<T, NP>::R][TallCfg<T, NP>::CN],
+                                                const Vec<T, TallCfg<T, NP>::R> &av,
+                                                const T *bsrc) {
+    using Cfg = TallCfg<T, NP>;
+#pragma unroll
+    for (int c0 = 0; c0 < Cfg::CN; c0 += Cfg::BV) {
+        const Vec<T, Cfg::BV> bv = ld_vec<T, Cfg::BV>(bsrc + c0);
+#pragma unroll
+        for (int c = 0; c < Cfg::BV; ++c)
+#pragma unroll
+            for (int r = 0; r < Cfg::R; ++r) acc[r][c0 + c] = fma(av.v[r], bv.v[c], acc[r][c0 + c]);
+    }
+}
+
+template <typename T, int NP>
+__global__ void __launch_bounds__(TallCfg<T, NP>::THREADS, 2)
+    tall_tma_kernel(const __grid_constant__ CUtensorMap tmA, const TallArgs a) {
+    using Cfg = TallCfg<T, NP>;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    T *sA = reinterpret_cast<T *>(smem_raw);
+    T *sB = sA + Cfg::STAGES * Cfg::A_STAGE;
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem_raw + Cfg::DATA_BYTES);
+    uint64_t *empty = full + Cfg::STAGES;
+    unsigned *flag = reinterpret_cast<unsigned *>(empty + Cfg::STAGES);
+    unsigned *abort_flag = flag + 1;
+
+    const int warp = threadIdx.x / 32;
+    const int lane = threadIdx.x % 32;
+    const int64_t slab = blockIdx.x;
+    const int split = blockIdx.y;
+    const int64_t k0 = (int64_t)split * a.kchunk;
+    const int64_t k1 = (k0 + a.kchunk < a.kp) ? k0 + a.kchunk : a.kp;
+    const int iters = (int)((k1 - k0) / Cfg::BKS);
+
+    if (threadIdx.x == 0) {
+        prefetch_tmap(&tmA);
+        for (int s = 0; s < Cfg::STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], Cfg::NWARPS);
+        }
+        *abort_flag = 0u;
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    if (warp == Cfg::NWARPS) {
+        // ---------------- producer warp: one elected lane issues the copies
+        if (lane == 0) {
+            const uint64_t pol_a = policy_evict_first();
+            const uint64_t pol_b = policy_evict_last();
+            const T *Bp = static_cast<const T *>(a.Bp);
+            for (int it = 0; it < iters; ++it) {
+                const int st = it % Cfg::STAGES;
+                if (it >= Cfg::STAGES) {
+                    if (!mbar_wait_bounded(&empty[st], ((it / Cfg::STAGES) & 1) ^ 1)) {
+                        atomicOr(a.status, kDevErrTimeout);
+                        break;
+                    }
+                }
+                const int64_t kk = k0 + (int64_t)it * Cfg::BKS;
+                mbar_arrive_expect_tx(&full[st], Cfg::STAGE_BYTES);
+                tma_load_2d(sA + st * Cfg::A_STAGE, &tmA, (int32_t)(slab * Cfg::BM), (int32_t)kk,
+                            &full[st], pol_a);
+                bulk_load(sB + st * Cfg::B_STAGE, Bp + kk * NP, Cfg::B_STAGE * (int)sizeof(T),
+                          &full[st], pol_b);
+            }
+        }
+        return;
+    }
+
+    // ---------------- consumer warps
+    const int wm = warp % Cfg::WM;
+    const int wk = warp / Cfg::WM;
+    const int g = lane / Cfg::LR;
+    const int lr = lane % Cfg::LR;
+    const int rloc = wm * Cfg::WROWS + lr * Cfg::R;  // first local row of this thread
+    const int cloc = g * Cfg::CN;                    // first column of this thread
+
+    T acc[Cfg::R][Cfg::CN];
+#pragma unroll
+    for (int r = 0; r < Cfg::R; ++r)
+#pragma unroll
+        for (int c = 0; c < Cfg::CN; ++c) acc[r][c] = T(0);
+
+    bool ok = true;
+    for (int it = 0; it < iters; ++it) {
+        const int st = it % Cfg::STAGES;
+        if (!mbar_wait_bounded(&full[st], (it / Cfg::STAGES) & 1)) {
+            ok = false;
+            break;
+        }
+        const T *As = sA + st * Cfg::A_STAGE;
+        const T *Bs = sB + st * Cfg::B_STAGE;
+#pragma unroll
+        for (int c = 0; c < Cfg::KPW; ++c) {
+            const int col = wk * Cfg::KPW + c;
+            const Vec<T, Cfg::R> av = ld_vec<T, Cfg::R>(As + col * Cfg::BM + rloc);
+            tall_fma_column<T, NP>(acc, av, Bs + col * NP + cloc);
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[st]);
+    }
+    if (!ok && lane == 0) {
+        atomicOr(a.status, kDevErrTimeout);
+        atomicOr(abort_flag, 1u);
+    }
+
+    // all stages consumed (or abandoned): every consumer warp gets here, since
+    // each wait above is bounded, so the named barrier cannot hang
+    named_barrier(1, Cfg::CONSUMERS);
+    if (*abort_flag != 0u) return;  // tile not written; the host sees TSMM_ERR_TIMEOUT
+    T *red = sA;
+#pragma unroll
+    for (int c = 0; c < Cfg::CN; ++c) {
+        Vec<T, Cfg::R> v;
+#pragma unroll
+        for (int r = 0; r < Cfg::R; ++r) v.v[r] = acc[r][c];
+        st_vec<T, Cfg::R>(red + (wk * NP + cloc + c) * Cfg::BM + rloc, v);
+    }
+    named_barrier(1, Cfg::CONSUMERS);
+    tall_finish<T, NP>(red, a, slab, split, threadIdx.x, flag);
+}
+
+// Same decomposition without TMA: for A pointers or leading dimensions that a
+// tensor map cannot describe (not 16-byte aligned).  Plain guarded loads.
+template <typename T, int NP>
+__global__ void __launch_bounds__(TallCfg<T, NP>::CONSUMERS, 2)
+    tall_generic_kernel(const TallArgs a) {
+    using Cfg = TallCfg<T, NP>;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    T *red = reinterpret_cast<T *>(smem_raw);
+    unsigned *flag = reinterpret_cast<unsigned *>(smem_raw + Cfg::RED * sizeof(T));
+
+    const int warp = threadIdx.x / 32;
+    const int lane = threadIdx.x % 32;
+    const int64_t slab = blockIdx.x;
+    const int split = blockIdx.y;
+    const int64_t k0 = (int64_t)split * a.kchunk;
+    const int64_t k1 = (k0 + a.kchunk < a.k) ? k0 + a.kchunk : a.k;
+    const int wm = warp % Cfg::WM;
+    const int wk = warp / Cfg::WM;
+    const int g = lane / Cfg::LR;
+    const int lr = lane % Cfg::LR;
+    const int rloc = wm * Cfg::WROWS + lr * Cfg::R;
+    const int cloc = g * Cfg::CN;
+    const int64_t i0 = slab * Cfg::BM + rloc;
+    const T *A = static_cast<const T *>(a.A);
+    const T *Bp = static_cast<const T *>(a.Bp);
+
+    T acc[Cfg::R][Cfg::CN];
+#pragma unroll
+    for (int r = 0; r < Cfg::R; ++r)
+#pragma unroll
+        for (int c = 0; c < Cfg::CN; ++c) acc[r][c] = T(0);
+
+    for (int64_t kb = k0; kb < k1; kb += Cfg::BKS) {
+        for (int c = 0; c < Cfg::KPW; ++c) {
+            const int64_t p = kb + wk * Cfg::KPW + c;
+            if (p >= k1) break;
+            Vec<T, Cfg::R> av;
+#pragma unroll
+            for (int r = 0; r < Cfg::R; ++r)
+                av.v[r] = (i0 + r < a.m) ? A[i0 + r + p * a.lda] : T(0);
+            tall_fma_column<T, NP>(acc, av, Bp + p * NP + cloc);
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < Cfg::CN; ++c) {
+        Vec<T, Cfg::R> v;
+#pragma unroll
+        for (int r = 0; r < Cfg::R; ++r) v.v[r] = acc[r][c];
+        st_vec<T, Cfg::R>(red + (wk * NP + cloc + c) * Cfg::BM + rloc, v);
+    }
+    named_barrier(1, Cfg::CONSUMERS);
+    tall_finish<T, NP>(red, a, slab, split, threadIdx.x, flag);
+}
+
+template <typename T, int NP>
+cudaError_t launch_tall_tma_t(const CUtensorMap *tmap, const TallArgs &a, cudaStream_t s) {
+    using Cfg = TallCfg<T, NP>;
+    static bool attr_done = false;  // per instantiation; benign if raced (idempotent)
+    if (!attr_done) {
+        cudaError_t e = cudaFuncSetAttribute(tall_tma_kernel<T, NP>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
+        if (e != cudaSuccess) return e;
+        attr_done = true;
+    }
+    dim3 grid((unsigned)a.slabs, (unsigned)a.splits);
+    tall_tma_kernel<T, NP><<<grid, Cfg::THREADS, Cfg::SMEM, s>>>(*tmap, a);
+    return cudaGetLastError();
+}
+
+template <typename T, int NP>
+cudaError_t launch_tall_generic_t(const TallArgs &a, cudaStream_t s) {
+    using Cfg = TallCfg<T, NP>;
+    const int smem = Cfg::RED * (int)sizeof(T) + 16;
+    static bool attr_done = false;
+    if (!attr_done) {
+        cudaError_t e = cudaFuncSetAttribute(tall_generic_kernel<T, NP>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        attr_done = true;
+    }
+    dim3 grid((unsigned)a.slabs, (unsigned)a.splits);
+    tall_generic_kernel<T, NP><<<grid, Cfg::CONSUMERS, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_tall_dispatch(bool tma, int np, const CUtensorMap *tmap, const TallArgs &a,
+                                 cudaStream_t s) {
+#define TSMM_TALL_CASE(NPV)                                                       \
+    case NPV:                                                                     \
+        return tma ? launch_tall_tma_t<T, NPV>(tmap, a, s)                        \
+                   : launch_tall_generic_t<T, NPV>(a, s);
+    switch (np) {
+        TSMM_TALL_CASE(1)
+        TSMM_TALL_CASE(2)
+        TSMM_TALL_CASE(4)
+        TSMM_TALL_CASE(8)
+        TSMM_TALL_CASE(16)
+        TSMM_TALL_CASE(32)
+        TSMM_TALL_CASE(64)
+        default:
+            return cudaErrorInvalidValue;
+    }
+#undef TSMM_TALL_CASE
+}
+
+}  // namespace tsmm

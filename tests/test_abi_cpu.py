@@ -1,0 +1,77 @@
+"""Host-side checks of the C ABI that need no GPU: the library loads, exports
+every entry point include/tsmm.h declares, and rejects bad arguments before
+touching the device."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_2208_08088_gb300 as tsmm
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    text = open(os.path.join(ROOT, "include", "tsmm.h")).read()
+    return sorted(set(re.findall(r"TSMM_API[^;(]*?\b(tsmm_\w+)\s*\(", text)))
+
+
+def test_header_declares_entry_points():
+    syms = declared_symbols()
+    for name in ("tsmm_pack_b", "tsmm_plan", "tsmm_execute", "tsmm_plan_destroy",
+                 "tsmm_packed_b_destroy", "tsmm_status_string"):
+        assert name in syms
+
+
+def test_library_exports_every_declared_symbol():
+    lib = ctypes.CDLL(tsmm.library_path)
+    missing = [s for s in declared_symbols() if not hasattr(lib, s)]
+    assert not missing, missing
+
+
+def test_exports_nothing_else():
+    """Hidden visibility: only the extern "C" entry points are exported."""
+    import subprocess
+    out = subprocess.run(["nm", "-D", "--defined-only", tsmm.library_path],
+                         capture_output=True, text=True, check=True).stdout
+    exported = {l.split()[-1] for l in out.splitlines() if " T " in l}
+    assert exported == set(declared_symbols())
+
+
+def test_status_strings_and_version():
+    for code, name in tsmm.STATUS.items():
+        assert tsmm.tsmm_status_string(code) == name
+    assert tsmm.tsmm_status_string(99) == "TSMM_ERR_UNKNOWN"
+    assert tsmm.tsmm_version() >= 100
+
+
+def test_argument_errors_before_device_work():
+    L = tsmm.lib
+    out = ctypes.c_void_p()
+    # plan: negative size, bad dtype, NULL out, unsupported shape
+    assert L.tsmm_plan(-1, 4, 4, 0, ctypes.byref(out)) == 1
+    assert L.tsmm_plan(4, 4, 4, 7, ctypes.byref(out)) == 1
+    assert L.tsmm_plan(4, 4, 4, 0, None) == 1
+    assert L.tsmm_plan(1000, 65, 129, 0, ctypes.byref(out)) == 2
+    # pack: NULL out, ldb < k, NULL B with nonzero size, misaligned B, unsupported
+    assert L.tsmm_pack_b(0, 8, 4, None, 8, None, None) == 1
+    assert L.tsmm_pack_b(0, 8, 4, 256, 7, None, ctypes.byref(out)) == 1
+    assert L.tsmm_pack_b(0, 8, 4, None, 8, None, ctypes.byref(out)) == 1
+    assert L.tsmm_pack_b(0, 8, 4, 258, 8, None, ctypes.byref(out)) == 4
+    assert L.tsmm_pack_b(1, 8, 4, 260, 8, None, ctypes.byref(out)) == 4
+    assert L.tsmm_pack_b(0, 129, 65, 256, 129, None, ctypes.byref(out)) == 2
+    assert out.value is None  # never written on failure
+    # execute / destroy / info with NULL handles
+    assert L.tsmm_execute(None, 1.0, None, 1, None, 0.0, None, 1, None) == 1
+    assert L.tsmm_plan_destroy(None) == 0
+    assert L.tsmm_packed_b_destroy(None) == 0
+    assert L.tsmm_plan_info(None, None, None, None, None, None) == 1
+    assert L.tsmm_plan_check(None) == 1
+    assert L.tsmm_plan_launches_per_execute(None) == 0
+
+
+def test_python_raises_tsmm_error():
+    with pytest.raises(tsmm.TsmmError) as ei:
+        tsmm.tsmm_plan(10, 100, 1000, tsmm.F32)
+    assert ei.value.status == 2

@@ -1,0 +1,253 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle, element
+by element, on seeded inputs at sizes that span several tiles and ragged tails.
+
+Acceptance (Eq. 1 with the componentwise bound of the library's contract):
+|C - C_ref| <= 4*k*u*(|alpha| |A||B| + |beta| |C0|), u = 2^-24 / 2^-53; and
+bit-exact equality on integer-valued inputs whose partial sums are exactly
+representable (entries in [-4, 4], dyadic alpha and beta)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2208_08088_gb300 as tsmm
+import tsmm_inputs as ti
+from gpu_util import assert_parity, run, to_device
+
+pytestmark = pytest.mark.gpu
+
+DT = [np.float32, np.float64]
+
+
+def gen(m, n, k, dtype, dist="uniform", seeds=(ti.SEED_A, ti.SEED_B, ti.SEED_C0)):
+    return (ti.matrix_np(m, k, seeds[0], dist, dtype), ti.matrix_np(k, n, seeds[1], dist, dtype),
+            ti.matrix_np(m, n, seeds[2], dist, dtype))
+
+
+# ------------------------------------------------------------- BASELINE config 1
+@pytest.mark.parametrize("dist", ["uniform", "integer"])
+@pytest.mark.parametrize("dtype", DT)
+def test_config1_2048x2048x16(dist, dtype):
+    """m = k = 2048, n = 16, alpha = 1.5, beta = 0.5, B packed once."""
+    A, B, C0 = gen(2048, 16, 2048, dtype, dist)
+    C, pl, _ = run(A, B, C0, 1.5, 0.5)
+    assert_parity(C, A, B, C0, 1.5, 0.5, exact=(dist == "integer"))
+
+
+# ------------------------------------------------------------- regime (i) sweep
+@pytest.mark.parametrize("dtype", DT)
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 8, 9, 16, 17, 31, 32, 33, 48, 63, 64])
+def test_tall_all_n_ragged(dtype, n):
+    """m, k not multiples of the tile sizes (128/64 rows, 32-column stages)."""
+    m, k = 1000, 777
+    A, B, C0 = gen(m, n, k, dtype)
+    C, pl, _ = run(A, B, C0, -1.25, 0.75)
+    assert pl.info()["regime"] == 1
+    assert_parity(C, A, B, C0, -1.25, 0.75)
+
+
+@pytest.mark.parametrize("dtype", DT)
+@pytest.mark.parametrize("m,n,k", [(1, 1, 1), (1, 16, 1), (3, 7, 2), (5, 64, 33), (129, 16, 31),
+                                   (128, 16, 32), (64, 64, 64), (257, 2, 4097)])
+def test_tall_small_and_edges(dtype, m, n, k):
+    A, B, C0 = gen(m, n, k, dtype)
+    C, _, _ = run(A, B, C0, 1.0, 1.0)
+    assert_parity(C, A, B, C0, 1.0, 1.0)
+
+
+@pytest.mark.parametrize("dtype", DT)
+@pytest.mark.parametrize("n", [1, 16, 64])
+def test_tall_split_k_integer_exact(dtype, n):
+    """Few m-slabs and long k force split-K (S > 1); integer inputs make the
+    result independent of the summation order, so it must be bit-exact."""
+    m, k = 300, 20000
+    A, B, C0 = gen(m, n, k, dtype, "integer")
+    C, pl, _ = run(A, B, C0, 1.5, 0.5)
+    assert pl.info()["splits"] > 1
+    assert_parity(C, A, B, C0, 1.5, 0.5, exact=True)
+
+
+@pytest.mark.parametrize("dtype", DT)
+def test_tall_split_k_uniform(dtype):
+    m, n, k = 700, 16, 30000
+    A, B, C0 = gen(m, n, k, dtype)
+    C, pl, _ = run(A, B, C0, 1.0, -1.0)
+    assert pl.info()["splits"] > 1
+    assert_parity(C, A, B, C0, 1.0, -1.0)
+
+
+@pytest.mark.parametrize("dtype", DT)
+def test_deterministic_repeats(dtype):
+    """Fixed-order split-K: repeated executions give identical bits."""
+    A, B, C0 = gen(500, 16, 9000, dtype)
+    outs, pl, _ = run(A, B, C0, 1.0, 0.5, repeats=3)
+    assert pl.info()["splits"] > 1
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[1], outs[2])
+
+
+# ------------------------------------------------------------- layouts / paths
+@pytest.mark.parametrize("dtype", DT)
+@pytest.mark.parametrize("n", [4, 16, 64])
+def test_padded_leading_dimensions_tma_path(dtype, n):
+    """lda, ldb, ldc larger than the matrix (16-byte multiples keep TMA); the
+    padding holds NaN and must never be read or written."""
+    m, k = 333, 515
+    A, B, C0 = gen(m, n, k, dtype)
+    C, _, _ = run(A, B, C0, 1.5, 0.5, lda=352, ldb=520, ldc=340)
+    assert_parity(C, A, B, C0, 1.5, 0.5)
+
+
+@pytest.mark.parametrize("dtype", DT)
+@pytest.mark.parametrize("n", [1, 16, 64])
+def test_unaligned_A_takes_plain_load_path(dtype, n):
+    """An odd lda (rows not 16-byte aligned) and an A pointer one element off
+    a 16-byte boundary: the kernel without TMA must give the same result."""
+    m, k = 301, 250
+    A, B, C0 = gen(m, n, k, dtype)
+    C1, _, _ = run(A, B, C0, 1.0, 1.0, lda=303)
+    assert_parity(C1, A, B, C0, 1.0, 1.0)
+    C2, _, _ = run(A, B, C0, 1.0, 1.0, a_offset=1)
+    assert_parity(C2, A, B, C0, 1.0, 1.0)
+
+
+@pytest.mark.parametrize("dtype", DT)
+def test_unaligned_integer_matches_tma_bitwise(dtype):
+    A, B, C0 = gen(640, 16, 3000, dtype, "integer")
+    C_tma, _, _ = run(A, B, C0, 1.5, 0.5)
+    C_gen, _, _ = run(A, B, C0, 1.5, 0.5, a_offset=1)
+    assert np.array_equal(C_tma, C_gen)
+    assert_parity(C_tma, A, B, C0, 1.5, 0.5, exact=True)
+
+
+# ------------------------------------------------------------- special cases
+@pytest.mark.parametrize("dtype", DT)
+@pytest.mark.parametrize("n,k", [(16, 100), (200, 64)])
+def test_alpha_zero_reads_neither_A_nor_B(dtype, n, k):
+    m = 150
+    A = np.full((m, k), np.nan, dtype=dtype, order="F")
+    B = np.asfortranarray(np.full((k, n), np.inf, dtype=dtype))
+    C0 = ti.matrix_np(m, n, 3, "uniform", dtype)
+    C, _, _ = run(A, B, C0, 0.0, 1.5)
+    np.testing.assert_array_equal(C, (C0.astype(np.float64) * 1.5).astype(dtype))
+
+
+@pytest.mark.parametrize("dtype", DT)
+@pytest.mark.parametrize("n,k", [(16, 100), (200, 64)])
+def test_beta_zero_overwrites_nan(dtype, n, k):
+    m = 150
+    A, B, _ = gen(m, n, k, dtype)
+    C, _, _ = run(A, B, None, 2.0, 0.0)
+    assert np.all(np.isfinite(C))
+    assert_parity(C, A, B, None, 2.0, 0.0)
+
+
+@pytest.mark.parametrize("dtype", DT)
+def test_k_zero_is_beta_scale(dtype):
+    m, n = 77, 9
+    C0 = ti.matrix_np(m, n, 3, "uniform", dtype)
+    A = np.zeros((m, 0), dtype=dtype, order="F")
+    B = np.zeros((0, n), dtype=dtype, order="F")
+    C, _, _ = run(A, B, C0, 1.0, 0.5)
+    np.testing.assert_array_equal(C, (C0.astype(np.float64) * 0.5).astype(dtype))
+
+
+@pytest.mark.parametrize("dtype", DT)
+def test_empty_m_or_n_is_noop(dtype):
+    for (m, n, k) in ((0, 16, 10), (10, 0, 10)):
+        pl = tsmm.plan(m, n, k, gpu_dtype(dtype))
+        dB = to_device(np.zeros((k, n), dtype=dtype, order="F"))
+        pb = tsmm.pack_b(dB)
+        dA = to_device(np.zeros((m, k), dtype=dtype, order="F"))
+        dC = to_device(np.zeros((m, n), dtype=dtype, order="F"))
+        tsmm.execute(pl, 1.0, dA, pb, 1.0, dC)
+        pl.check()
+        assert pl.launches_per_execute() == 0
+
+
+def gpu_dtype(dtype):
+    return torch.float32 if dtype == np.float32 else torch.float64
+
+
+@pytest.mark.parametrize("dtype", DT)
+def test_ieee_specials_propagate(dtype):
+    m, n, k = 130, 4, 70
+    A, B, C0 = gen(m, n, k, dtype)
+    A = A.copy(order="F")
+    A[5, 3] = np.inf
+    A[77, 10] = np.nan
+    C, _, _ = run(A, B, C0, 1.0, 1.0)
+    assert_parity(C, A, B, C0, 1.0, 1.0)
+
+
+# ------------------------------------------------------------- regime (ii)
+@pytest.mark.parametrize("dtype", DT)
+@pytest.mark.parametrize("k", [1, 4, 7, 32, 37, 64, 128])
+def test_rankk_ragged(dtype, k):
+    m, n = 1000, 300
+    A, B, C0 = gen(m, n, k, dtype)
+    C, pl, _ = run(A, B, C0, 1.0, 1.0)
+    assert pl.info()["regime"] == 2
+    assert_parity(C, A, B, C0, 1.0, 1.0)
+
+
+@pytest.mark.parametrize("dtype", DT)
+def test_rankk_integer_exact_and_padded(dtype):
+    m, n, k = 513, 257, 100
+    A, B, C0 = gen(m, n, k, dtype, "integer")
+    C, _, _ = run(A, B, C0, 1.5, 0.5, lda=520, ldb=104, ldc=516)
+    assert_parity(C, A, B, C0, 1.5, 0.5, exact=True)
+    C2, _, _ = run(A, B, C0, 1.5, 0.5, lda=515, ldc=514, a_offset=1, c_offset=1)
+    assert np.array_equal(C, C2)
+
+
+# ------------------------------------------------------------- packing + ABI errors
+@pytest.mark.parametrize("dtype", DT)
+@pytest.mark.parametrize("k,n", [(1, 1), (33, 5), (100, 64), (7, 65), (128, 300)])
+def test_pack_roundtrip_bitwise(dtype, k, n):
+    """Unpacking the packed storage with a reader written from the layout
+    documented in include/tsmm.h reproduces B bit for bit, with +0 padding."""
+    B = ti.matrix_np(k, n, 9, "uniform", dtype)
+    pb = tsmm.pack_b(to_device(B, ld=k + 3))
+    info = pb.info()
+    flat = pb.read()
+    kp, w, nt = info["kp"], info["w"], info["ntiles"]
+    assert flat.size == kp * w * nt and kp >= k and w * nt >= n
+    tiles = flat.reshape(nt, kp, w)
+    full = np.concatenate([tiles[t] for t in range(nt)], axis=1)  # kp x (nt*w)
+    assert np.ascontiguousarray(full[:k, :n]).tobytes() == np.ascontiguousarray(B).tobytes()
+    pad = full.copy()
+    pad[:k, :n] = 0
+    assert np.all(pad == 0) and not np.any(np.signbit(pad))
+
+
+def test_mismatch_and_misaligned_errors():
+    B = to_device(ti.matrix_np(100, 16, 1, "uniform", np.float32))
+    pb = tsmm.pack_b(B)
+    A = to_device(ti.matrix_np(50, 101, 1, "uniform", np.float32))
+    C = to_device(np.zeros((50, 16), dtype=np.float32, order="F"))
+    with pytest.raises(tsmm.TsmmError) as e:
+        tsmm.execute(tsmm.plan(50, 16, 101, torch.float32), 1.0, A, pb, 0.0, C)
+    assert e.value.status == 3
+    A64 = to_device(ti.matrix_np(50, 100, 1, "uniform", np.float64))
+    with pytest.raises(tsmm.TsmmError) as e:
+        tsmm.execute(tsmm.plan(50, 16, 100, torch.float64), 1.0, A64, pb, 0.0, C)
+    assert e.value.status == 3
+    pl = tsmm.plan(50, 16, 100, torch.float32)
+    with pytest.raises(tsmm.TsmmError) as e:  # C pointer not 4-byte aligned
+        tsmm.tsmm_execute(pl.handle, 1.0, A.data_ptr(), 50, pb.handle, 0.0, C.data_ptr() + 2, 50)
+    assert e.value.status == 4
+    with pytest.raises(tsmm.TsmmError) as e:  # lda < m
+        tsmm.tsmm_execute(pl.handle, 1.0, A.data_ptr(), 49, pb.handle, 0.0, C.data_ptr(), 50)
+    assert e.value.status == 1
+
+
+def test_plan_reuse_across_A_pointers():
+    """The plan caches its TMA descriptor per A pointer; a new A must be seen."""
+    m, n, k = 400, 8, 600
+    A1, B, C0 = gen(m, n, k, np.float32)
+    A2 = ti.matrix_np(m, k, 77, "uniform", np.float32)
+    pl = tsmm.plan(m, n, k, torch.float32)
+    pb = tsmm.pack_b(to_device(B))
+    for A in (A1, A2, A1):
+        C, _, _ = run(A, B, C0, 1.0, 0.0, plan=pl, pb=pb)
+        assert_parity(C, A, B, None, 1.0, 0.0)

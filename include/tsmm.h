@@ -180,6 +180,49 @@ TSMM_API tsmm_status tsmm_plan_check(tsmm_plan_t plan);
 /* Number of kernel launches `tsmm_execute` with this plan enqueues (for accounting). */
 TSMM_API int tsmm_plan_launches_per_execute(tsmm_plan_t plan);
 
+/* Size of the library's built-in device scratch used by tsmm_execute_noalloc. */
+#define TSMM_NOALLOC_SCRATCH_BYTES (32u << 20)
+
+/*
+ * tsmm_execute_noalloc -- C = alpha * A * B + beta * C0 for regime (i) shapes
+ * (n <= 64) without allocating any device memory.  The paper has no
+ * counterpart: this entry point exists for callers that cannot call cudaMalloc
+ * -- code whose device memory is owned and budgeted by a host framework (an
+ * inference engine or plug-in host that forbids allocations of its own), and
+ * latency-critical loops that cannot afford cudaMalloc's implicit device
+ * synchronisation.  Such callers cannot use tsmm_pack_b or tsmm_plan, which
+ * allocate.
+ *
+ * The caller passes the unpacked B (k x n, column-major, ldb) together with A
+ * and C exactly as for tsmm_execute.  Every call packs B and runs the same
+ * split-K kernel as tsmm_execute, with the packed B, the split-K partial
+ * tiles, the arrival counters and the error word all placed in one file-scope
+ * device array of TSMM_NOALLOC_SCRATCH_BYTES (32 MiB) that every GPU loading
+ * the library holds until the process exits.  The k split is reduced so the
+ * partial tiles fit; sizes whose packed B (k rounded up to 32, times n rounded
+ * up to a power of two, times the element size) plus one arrival counter per
+ * 128 (F32) / 64 (F64) rows of m do not fit return TSMM_ERR_UNSUPPORTED_SHAPE
+ * before any device work, as do shapes with n > 64.
+ *
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current, so make the first call on
+ * a device before any stream capture.  All calls share the one array and it
+ * keeps the previous call's contents: each call clears the counters and error
+ * word it needs on `stream` first.  Calls whose work can overlap on the GPU
+ * (different streams, or different host threads on the same device) race on
+ * the array and give wrong results; serialise them.  Device-side timeouts of
+ * this entry point are not reported (there is no plan to check); the output
+ * tile of a block that gave up is left unwritten.
+ *
+ * Errors: INVALID_ARG, UNSUPPORTED_SHAPE, MISALIGNED, CUDA, as for
+ * tsmm_pack_b and tsmm_execute.  Enqueues up to three operations on `stream`
+ * (a memset, the pack, the TSMM kernel) and returns without waiting.
+ */
+TSMM_API tsmm_status tsmm_execute_noalloc(tsmm_dtype dtype, int64_t m, int64_t n, int64_t k,
+                                          double alpha, const void *A_dev, int64_t lda,
+                                          const void *B_dev, int64_t ldb, double beta,
+                                          void *C_dev, int64_t ldc, tsmm_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

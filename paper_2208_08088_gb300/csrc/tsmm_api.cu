@@ -49,6 +49,10 @@ int current_device() {
     return dev;
 }
 
+}  // namespace
+
+namespace tsmm {
+
 // Split-K choice for regime (i): minimise a wave-quantised time model
 //   T(S) = ceil(slabs*S / resident) * (ceil(kstages / S) + overhead)
 // where `resident` thread blocks run at once (2 per SM) and `overhead` is the
@@ -72,7 +76,7 @@ int choose_splits(int64_t slabs, int64_t kstages, int num_sms, int64_t max_split
     return (int)best_s;
 }
 
-}  // namespace
+}  // namespace tsmm
 
 extern "C" {
 

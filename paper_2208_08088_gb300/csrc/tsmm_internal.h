@@ -113,6 +113,9 @@ struct RankArgs {
 };
 cudaError_t launch_rankk(tsmm_dtype dt, const RankArgs &a, cudaStream_t s);
 
+// Split-K factor of the regime (i) kernel (planner model in tsmm_api.cu).
+int choose_splits(int64_t slabs, int64_t kstages, int num_sms, int64_t max_splits);
+
 cudaError_t launch_pack_b(tsmm_dtype dt, int64_t k, int64_t n, const void *B, int64_t ldb,
                           void *dst, int64_t kp, int64_t w, int64_t ntiles, cudaStream_t s);
 cudaError_t launch_scale(tsmm_dtype dt, int64_t m, int64_t n, double beta, void *C, int64_t ldc,

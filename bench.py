@@ -56,6 +56,11 @@ def parse():
     p.add_argument("--dtype", choices=["f32", "f64"], default="f32")
     p.add_argument("--workload", choices=["tall", "rankk"], default="tall")
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--size", type=int, default=None,
+                   help="profiling/small runs: m = k (tall) or m = n (rankk) instead of the workload's")
+    p.add_argument("--only", type=int, default=None,
+                   help="profiling/small runs: keep only this n (tall) or k (rankk)")
+    p.add_argument("--beta", type=float, default=None, help="profiling/small runs: one beta only")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     return p.parse_args()
@@ -72,12 +77,20 @@ def load_peaks():
 
 def workload_points(args):
     """(m, n, k, beta) per launch of one step."""
+    betas = SWEEP_BETA if args.beta is None else [args.beta]
     if args.workload == "tall":
-        return [(32768, n, 32768, b) for n in SWEEP_N for b in SWEEP_BETA]
-    return [(16384, 16384, k, 1.0) for k in RANKK_K]
+        s = args.size or 32768
+        ns = SWEEP_N if args.only is None else [args.only]
+        return [(s, n, s, b) for n in ns for b in betas]
+    s = args.size or 16384
+    ks = RANKK_K if args.only is None else [args.only]
+    return [(s, s, k, 1.0 if args.beta is None else args.beta) for k in ks]
 
 
 def workload_name(args):
+    if args.size or args.only or args.beta is not None:
+        return "reduced case for profiling: " + ", ".join(
+            f"m={m} n={n} k={k} beta={b}" for (m, n, k, b) in workload_points(args))
     if args.workload == "tall":
         return (f"memory-bound sweep {args.dtype.upper()} m=k=32768, n in {SWEEP_N}, "
                 f"beta in {{0,1}}, alpha=1, B pre-packed and reused")

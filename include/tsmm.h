@@ -98,7 +98,7 @@ TSMM_API int tsmm_version(void);
  *
  * Packed layout (private to the library, described for test readers): the
  * n columns are cut into `ntiles` tiles of `w` columns (regime (i): one tile,
- * w = the kernel's padded column count; regime (ii): w = 128).  Tile t is a
+ * w = the kernel's padded column count; regime (ii): w = 64).  Tile t is a
  * row-major kp x w block (kp = k rounded up to the kernel's k granule) at
  * element offset t*kp*w; element (p, jj) of tile t holds B[p, t*w + jj], and is
  * +0.0 where p >= k or t*w + jj >= n.
@@ -179,6 +179,70 @@ TSMM_API tsmm_status tsmm_plan_check(tsmm_plan_t plan);
 
 /* Number of kernel launches `tsmm_execute` with this plan enqueues (for accounting). */
 TSMM_API int tsmm_plan_launches_per_execute(tsmm_plan_t plan);
+
+/*
+ * One problem of a grouped execution: the arguments of one tsmm_execute call.
+ */
+typedef struct tsmm_group_item {
+    tsmm_plan_t plan;
+    double alpha;
+    const void *A_dev;
+    int64_t lda;
+    tsmm_packed_b pb;
+    double beta;
+    void *C_dev;
+    int64_t ldc;
+} tsmm_group_item;
+
+/*
+ * tsmm_execute_grouped -- run `count` independent TSMMs (uneven shapes, each
+ * with its own plan, packed B, alpha, beta, A and C) with as few kernel
+ * launches as possible: the grouped execution of many pre-packed products that
+ * the paper's reuse argument (Section III) motivates.  Regime (i) problems
+ * whose A is 16-byte aligned with lda*sizeof(element) a multiple of 16 are
+ * batched per (dtype, padded column count) into launches of one persistent
+ * kernel, at most 48 problems per launch, whose blocks walk the problems' work
+ * items (m-slab x k-split) and keep their TMA pipeline running across item
+ * boundaries; any other problem runs as its own tsmm_execute launch on the same
+ * stream.  Results equal tsmm_execute's bit for bit.  Every item is validated
+ * as tsmm_execute would before anything is launched; two items may not share a
+ * plan (INVALID_ARG), since a plan's split-K workspace serves one problem at a
+ * time.  Asynchronous on `stream`.
+ */
+TSMM_API tsmm_status tsmm_execute_grouped(const tsmm_group_item *items, int count,
+                                          tsmm_stream_t stream);
+
+/*
+ * tsmm_autotune -- the performance evaluator of Section III: time candidate
+ * execution plans for this shape on the caller's operands and keep the
+ * fastest.  For regime (i) the candidates are split-K factors (the planner's
+ * model evaluated for 1..4 resident blocks per SM, its halves and doubles, no
+ * split, and factors that fill whole waves of the GPU); each candidate runs
+ * once untimed and `reps` times between CUDA events on `stream` with alpha = 1,
+ * beta = 0, so C is overwritten.  Blocks until the timing is done.  The
+ * winning split count is recorded in the process-wide plan cache, which later
+ * tsmm_plan calls for the same (dtype, m, n, k) on a GPU with the same SM count
+ * reuse; a new plan with it is returned in *out.  Regime (ii) shapes have no
+ * tuned parameter yet and return the default plan.  Errors: as tsmm_plan and
+ * tsmm_execute; INVALID_ARG for reps outside 1..1000.
+ */
+TSMM_API tsmm_status tsmm_autotune(int64_t m, int64_t n, int64_t k, tsmm_dtype dtype,
+                                   const void *A_dev, int64_t lda, tsmm_packed_b pb, void *C_dev,
+                                   int64_t ldc, tsmm_stream_t stream, int reps, tsmm_plan_t *out);
+
+/*
+ * The plan cache (the install-time record of tuned choices).  Text format, one
+ * entry per line: `f32|f64 m n k sm_count splits`; lines starting with '#' are
+ * comments.  If the environment variable TSMM_PLAN_CACHE names a file, it is
+ * loaded on first use.  load merges a file into the cache (INVALID_ARG if the
+ * file is missing or malformed, leaving the cache unchanged); save writes the
+ * whole cache; clear empties it; size returns the number of entries.  The
+ * cache is guarded by a mutex and shared by all threads of the process.
+ */
+TSMM_API tsmm_status tsmm_plan_cache_load(const char *path);
+TSMM_API tsmm_status tsmm_plan_cache_save(const char *path);
+TSMM_API tsmm_status tsmm_plan_cache_clear(void);
+TSMM_API int64_t tsmm_plan_cache_size(void);
 
 /* Size of the library's built-in device scratch used by tsmm_execute_noalloc. */
 #define TSMM_NOALLOC_SCRATCH_BYTES (32u << 20)

@@ -28,7 +28,9 @@ __all__ = [
     "TsmmError", "F32", "F64", "lib", "library_path",
     "tsmm_status_string", "tsmm_version", "tsmm_pack_b", "tsmm_packed_b_destroy",
     "tsmm_packed_b_info", "tsmm_packed_b_read", "tsmm_plan", "tsmm_plan_destroy", "tsmm_plan_info", "tsmm_execute",
-    "tsmm_plan_check", "tsmm_plan_launches_per_execute",
+    "tsmm_plan_check", "tsmm_plan_launches_per_execute", "tsmm_autotune",
+    "tsmm_plan_cache_load", "tsmm_plan_cache_save", "tsmm_plan_cache_clear", "tsmm_plan_cache_size",
+    "autotune", "execute_grouped", "tsmm_execute_grouped", "GroupItem",
     "PackedB", "Plan", "pack_b", "plan", "execute", "colmajor", "ld_of",
 ]
 
@@ -46,6 +48,13 @@ class TsmmError(RuntimeError):
     def __init__(self, status: int, where: str):
         self.status = status
         super().__init__(f"{where}: {STATUS.get(status, status)}")
+
+
+class GroupItem(ctypes.Structure):
+    """struct tsmm_group_item of include/tsmm.h."""
+    _fields_ = [("plan", ctypes.c_void_p), ("alpha", ctypes.c_double), ("A_dev", ctypes.c_void_p),
+                ("lda", ctypes.c_int64), ("pb", ctypes.c_void_p), ("beta", ctypes.c_double),
+                ("C_dev", ctypes.c_void_p), ("ldc", ctypes.c_int64)]
 
 
 def _load():
@@ -81,6 +90,17 @@ def _load():
     L.tsmm_plan_check.argtypes = [vp]
     L.tsmm_plan_launches_per_execute.restype = ci
     L.tsmm_plan_launches_per_execute.argtypes = [vp]
+    L.tsmm_execute_grouped.restype = ci
+    L.tsmm_execute_grouped.argtypes = [ctypes.POINTER(GroupItem), ci, vp]
+    L.tsmm_autotune.restype = ci
+    L.tsmm_autotune.argtypes = [i64, i64, i64, ci, vp, i64, vp, vp, i64, vp, ci, ctypes.POINTER(vp)]
+    for name in ("tsmm_plan_cache_load", "tsmm_plan_cache_save"):
+        getattr(L, name).restype = ci
+        getattr(L, name).argtypes = [ctypes.c_char_p]
+    L.tsmm_plan_cache_clear.restype = ci
+    L.tsmm_plan_cache_clear.argtypes = []
+    L.tsmm_plan_cache_size.restype = i64
+    L.tsmm_plan_cache_size.argtypes = []
     return L
 
 
@@ -159,6 +179,38 @@ def tsmm_plan_check(plan: int) -> None:
 
 def tsmm_plan_launches_per_execute(plan: int) -> int:
     return int(lib.tsmm_plan_launches_per_execute(plan))
+
+
+def tsmm_execute_grouped(items, stream: int = 0) -> None:
+    """items: sequence of (plan, alpha, A_dev, lda, pb, beta, C_dev, ldc) tuples of raw handles."""
+    arr = (GroupItem * max(1, len(items)))()
+    for i, (pl, alpha, A, lda, pb, beta, C, ldc) in enumerate(items):
+        arr[i] = GroupItem(pl, float(alpha), A or None, lda, pb, float(beta), C or None, ldc)
+    _check(lib.tsmm_execute_grouped(arr, len(items), stream or None), "tsmm_execute_grouped")
+
+
+def tsmm_autotune(m: int, n: int, k: int, dtype: int, A_dev: int, lda: int, pb: int, C_dev: int,
+                  ldc: int, stream: int = 0, reps: int = 5) -> int:
+    out = ctypes.c_void_p()
+    _check(lib.tsmm_autotune(m, n, k, dtype, A_dev or None, lda, pb, C_dev or None, ldc,
+                             stream or None, reps, ctypes.byref(out)), "tsmm_autotune")
+    return out.value
+
+
+def tsmm_plan_cache_load(path: str) -> None:
+    _check(lib.tsmm_plan_cache_load(os.fsencode(path)), "tsmm_plan_cache_load")
+
+
+def tsmm_plan_cache_save(path: str) -> None:
+    _check(lib.tsmm_plan_cache_save(os.fsencode(path)), "tsmm_plan_cache_save")
+
+
+def tsmm_plan_cache_clear() -> None:
+    _check(lib.tsmm_plan_cache_clear(), "tsmm_plan_cache_clear")
+
+
+def tsmm_plan_cache_size() -> int:
+    return int(lib.tsmm_plan_cache_size())
 
 
 # ------------------------------------------------------------------ torch layer
@@ -270,6 +322,28 @@ def pack_b(B, stream=None) -> PackedB:
 def plan(m: int, n: int, k: int, dtype) -> Plan:
     dt = dtype if isinstance(dtype, int) else _dtype_code(dtype)
     return Plan(tsmm_plan(m, n, k, dt), m, n, k, dt)
+
+
+def execute_grouped(problems, stream=None) -> None:
+    """problems: sequence of (plan, alpha, A, pb, beta, C) with column-major CUDA
+    tensors; all run with as few launches as the library can manage."""
+    items = []
+    for (p, alpha, A, pb, beta, C) in problems:
+        lda = ld_of(A) if p.m > 0 and p.k > 0 else max(1, p.m)
+        items.append((p.handle, alpha, A.data_ptr() if A.numel() else 0, lda, pb.handle, beta,
+                      C.data_ptr() if C.numel() else 0, ld_of(C) if p.n > 0 else max(1, p.m)))
+    tsmm_execute_grouped(items, _stream_handle(stream))
+
+
+def autotune(A, pb: PackedB, C, reps: int = 5, stream=None) -> Plan:
+    """Time candidate plans on these operands (C is overwritten), remember the
+    winner in the plan cache and return a plan that uses it."""
+    m, k = A.shape
+    n = C.shape[1]
+    dt = _dtype_code(A.dtype)
+    h = tsmm_autotune(m, n, k, dt, A.data_ptr(), ld_of(A), pb.handle, C.data_ptr(), ld_of(C),
+                      _stream_handle(stream), reps)
+    return Plan(h, m, n, k, dt)
 
 
 def execute(p: Plan, alpha: float, A, pb: PackedB, beta: float, C, stream=None) -> None:

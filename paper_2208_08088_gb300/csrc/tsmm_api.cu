@@ -55,11 +55,12 @@ namespace tsmm {
 
 // Split-K choice for regime (i): minimise a wave-quantised time model
 //   T(S) = ceil(slabs*S / resident) * (ceil(kstages / S) + overhead)
-// where `resident` thread blocks run at once (2 per SM) and `overhead` is the
-// per-block fixed cost (pipeline fill, reduction, epilogue) in stage units.
-// Smallest S wins ties, which also keeps the workspace small.
-int choose_splits(int64_t slabs, int64_t kstages, int num_sms, int64_t max_splits) {
-    const int64_t resident = 2LL * num_sms;
+// where `resident` thread blocks run at once (per SM, times the SM count) and
+// `overhead` is the per-block fixed cost (pipeline fill, reduction, epilogue)
+// in stage units.  Smallest S wins ties, which also keeps the workspace small.
+int choose_splits(int64_t slabs, int64_t kstages, int num_sms, int64_t max_splits,
+                  int per_sm) {
+    const int64_t resident = (int64_t)per_sm * num_sms;
     const int64_t overhead = 4;
     int64_t best_s = 1;
     double best_t = -1.0;
@@ -177,6 +178,22 @@ tsmm_status tsmm_packed_b_read(tsmm_packed_b pb, void *host_dst, size_t bytes) {
 
 tsmm_status tsmm_plan(int64_t m, int64_t n, int64_t k, tsmm_dtype dtype, tsmm_plan_t *out) {
     if (!out || !valid_dtype(dtype) || m < 0 || n < 0 || k < 0) return TSMM_ERR_INVALID_ARG;
+    int dev = current_device();
+    int sms = 0;
+    if (dev >= 0 && cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        sms = 0;
+    // a tuned choice recorded in the plan cache wins over the heuristic
+    const int cached = plan_cache_lookup(dtype, m, n, k, sms);
+    return create_plan(m, n, k, dtype, cached, out);
+}
+
+}  // extern "C"
+
+namespace tsmm {
+
+tsmm_status create_plan(int64_t m, int64_t n, int64_t k, tsmm_dtype dtype, int forced_splits,
+                        tsmm_plan_t *out) {
+    if (!out || !valid_dtype(dtype) || m < 0 || n < 0 || k < 0) return TSMM_ERR_INVALID_ARG;
     const int regime = regime_of(k, n);
     if (regime == 0) return TSMM_ERR_UNSUPPORTED_SHAPE;
     const int dev = current_device();
@@ -207,7 +224,12 @@ tsmm_status tsmm_plan(int64_t m, int64_t n, int64_t k, tsmm_dtype dtype, tsmm_pl
         const int64_t per_split = (int64_t)p->np * p->slabs * p->bm * (int64_t)es;
         int64_t max_splits = 65535;
         if (per_split > 0) max_splits = std::min<int64_t>(max_splits, (512LL << 20) / per_split);
-        int s = (kstages > 0 && p->slabs > 0) ? choose_splits(p->slabs, kstages, sms, max_splits) : 1;
+        const int per_sm = tall_resident_blocks(dtype == TSMM_F64, p->np);
+        int s = (kstages > 0 && p->slabs > 0)
+                    ? choose_splits(p->slabs, kstages, sms, max_splits, per_sm)
+                    : 1;
+        if (forced_splits > 0)
+            s = (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)forced_splits, kstages, max_splits}));
         const int64_t chunk_stages = kstages > 0 ? (kstages + s - 1) / s : 1;
         p->kchunk = chunk_stages * kTallBKS;
         p->splits = kstages > 0 ? (int)((kstages + chunk_stages - 1) / chunk_stages) : 1;
@@ -244,6 +266,10 @@ tsmm_status tsmm_plan(int64_t m, int64_t n, int64_t k, tsmm_dtype dtype, tsmm_pl
     *out = p;
     return TSMM_OK;
 }
+
+}  // namespace tsmm
+
+extern "C" {
 
 tsmm_status tsmm_plan_destroy(tsmm_plan_t p) {
     if (!p) return TSMM_OK;
@@ -292,22 +318,6 @@ tsmm_status tsmm_execute(tsmm_plan_t p, double alpha, const void *A_dev, int64_t
     }
     if (!use_ab) return cuda_status(launch_scale(p->dtype, m, n, beta, C_dev, ldc, s));
 
-    if (p->regime == 2) {
-        RankArgs a;
-        a.m = m;
-        a.n = n;
-        a.k = k;
-        a.lda = lda;
-        a.ldc = ldc;
-        a.kp = pb->kp;
-        a.A = A_dev;
-        a.Bp = pb->data;
-        a.C = C_dev;
-        a.alpha = alpha;
-        a.beta = beta;
-        return cuda_status(launch_rankk(p->dtype, a, s));
-    }
-
     TallArgs a;
     a.m = m;
     a.n = n;
@@ -330,6 +340,7 @@ tsmm_status tsmm_execute(tsmm_plan_t p, double alpha, const void *A_dev, int64_t
     const bool tma = aligned(A_dev, 16) && ((lda * (int64_t)es) % 16 == 0) && m < INT_MAX &&
                      k < INT_MAX && (lda * (int64_t)es) < (1LL << 40) && encoder() != nullptr;
     if (tma && (p->tmap_ptr != A_dev || p->tmap_lda != lda)) {
+        // box: bm rows x 32 columns (the regime (i) stage and the regime (ii) k chunk)
         const cuuint64_t gdim[2] = {(cuuint64_t)m, (cuuint64_t)k};
         const cuuint64_t gstride[1] = {(cuuint64_t)(lda * (int64_t)es)};
         const cuuint32_t box[2] = {(cuuint32_t)p->bm, (cuuint32_t)kTallBKS};
@@ -347,6 +358,46 @@ tsmm_status tsmm_execute(tsmm_plan_t p, double alpha, const void *A_dev, int64_t
         }
         p->tmap_ptr = A_dev;
         p->tmap_lda = lda;
+    }
+    if (p->regime == 2) {
+        RankArgs ra;
+        ra.m = m;
+        ra.n = n;
+        ra.k = k;
+        ra.lda = lda;
+        ra.ldc = ldc;
+        ra.kp = pb->kp;
+        ra.A = A_dev;
+        ra.Bp = pb->data;
+        ra.C = C_dev;
+        ra.alpha = alpha;
+        ra.beta = beta;
+        ra.num_sms = p->num_sms;
+        // C0 tile prefetch by TMA: needs the same 16-byte rules for C
+        const bool tmc = tma && beta != 0.0 && aligned(C_dev, 16) &&
+                         ((ldc * (int64_t)es) % 16 == 0) && n < INT_MAX &&
+                         (ldc * (int64_t)es) < (1LL << 40);
+        if (tmc && (p->tmapc_ptr != C_dev || p->tmapc_ldc != ldc)) {
+            const cuuint64_t gdim[2] = {(cuuint64_t)m, (cuuint64_t)n};
+            const cuuint64_t gstride[1] = {(cuuint64_t)(ldc * (int64_t)es)};
+            const cuuint32_t box[2] = {(cuuint32_t)p->bm, (cuuint32_t)kRankNT};
+            const cuuint32_t estr[2] = {1, 1};
+            CUresult r = encoder()(&p->tmapc,
+                                   p->dtype == TSMM_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                                        : CU_TENSOR_MAP_DATA_TYPE_FLOAT64,
+                                   2, C_dev, gdim, gstride, box, estr,
+                                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            if (r != CUDA_SUCCESS) {
+                p->tmapc_ptr = nullptr;
+                return TSMM_ERR_CUDA;
+            }
+            p->tmapc_ptr = C_dev;
+            p->tmapc_ldc = ldc;
+        }
+        return cuda_status(launch_rankk(p->dtype, tma ? &p->tmap : nullptr, tmc ? &p->tmapc : nullptr,
+                                        ra, p->status, s));
     }
     cudaError_t e = p->dtype == TSMM_F32 ? launch_tall_f32(tma, p->np, &p->tmap, a, s)
                                          : launch_tall_f64(tma, p->np, &p->tmap, a, s);

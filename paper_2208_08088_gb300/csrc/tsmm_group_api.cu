@@ -1,0 +1,154 @@
+// tsmm_execute_grouped: many pre-packed TSMMs in as few launches as possible.
+// Regime (i) problems whose A a tensor map can describe are batched, per dtype
+// and padded column count, into launches of the grouped persistent kernel (up
+// to kGroupMax problems each); every other problem (regime (ii), alpha = 0,
+// k = 0, unaligned A) is executed by its own tsmm_execute launch on the same
+// stream.
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <climits>
+#include <map>
+#include <memory>
+#include <set>
+#include <utility>
+#include <vector>
+
+#include "tsmm_group.cuh"
+
+namespace tsmm {
+cudaError_t launch_grouped_f32(int np, const GroupParams &gp, int num_sms, cudaStream_t s);
+cudaError_t launch_grouped_f64(int np, const GroupParams &gp, int num_sms, cudaStream_t s);
+}  // namespace tsmm
+
+using namespace tsmm;
+
+namespace {
+
+PFN_cuTensorMapEncodeTiled_v12000 encoder_grouped() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            p = nullptr;
+        return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }();
+    return fn;
+}
+
+bool is_aligned(const void *p, size_t a) { return reinterpret_cast<uintptr_t>(p) % a == 0; }
+
+// Same argument rules as tsmm_execute.
+tsmm_status validate(const tsmm_group_item &it) {
+    tsmm_plan_t p = it.plan;
+    tsmm_packed_b pb = it.pb;
+    if (!p || !pb) return TSMM_ERR_INVALID_ARG;
+    if (pb->dtype != p->dtype || pb->k != p->k || pb->n != p->n || pb->device != p->device)
+        return TSMM_ERR_MISMATCH;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return TSMM_ERR_CUDA;
+    if (dev != p->device) return TSMM_ERR_MISMATCH;
+    if (it.lda < std::max<int64_t>(1, p->m) || it.ldc < std::max<int64_t>(1, p->m))
+        return TSMM_ERR_INVALID_ARG;
+    if (p->m == 0 || p->n == 0) return TSMM_OK;
+    const bool use_ab = it.alpha != 0.0 && p->k > 0;
+    if (!it.C_dev || (use_ab && !it.A_dev)) return TSMM_ERR_INVALID_ARG;
+    const size_t es = dtype_size(p->dtype);
+    if (!is_aligned(it.C_dev, es) || (use_ab && !is_aligned(it.A_dev, es))) return TSMM_ERR_MISALIGNED;
+    return TSMM_OK;
+}
+
+bool groupable(const tsmm_group_item &it) {
+    tsmm_plan_t p = it.plan;
+    const size_t es = dtype_size(p->dtype);
+    const bool alpha_zero = it.alpha == 0.0 ||
+                            (p->dtype == TSMM_F32 && static_cast<float>(it.alpha) == 0.0f);
+    return p->regime == 1 && p->m > 0 && p->n > 0 && p->k > 0 && !alpha_zero &&
+           is_aligned(it.A_dev, 16) && (it.lda * (int64_t)es) % 16 == 0 && p->m < INT_MAX &&
+           p->k < INT_MAX && (it.lda * (int64_t)es) < (1LL << 40) && encoder_grouped() != nullptr;
+}
+
+}  // namespace
+
+extern "C" tsmm_status tsmm_execute_grouped(const tsmm_group_item *items, int count,
+                                            tsmm_stream_t stream) {
+    if (count < 0 || (count > 0 && !items)) return TSMM_ERR_INVALID_ARG;
+    std::set<tsmm_plan_t> seen;
+    for (int i = 0; i < count; ++i) {
+        tsmm_status st = validate(items[i]);
+        if (st != TSMM_OK) return st;
+        if (!seen.insert(items[i].plan).second) return TSMM_ERR_INVALID_ARG;  // shared workspace
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // classes of groupable problems: (dtype, np) -> item indices
+    std::map<std::pair<int, int>, std::vector<int>> classes;
+    for (int i = 0; i < count; ++i) {
+        if (groupable(items[i])) {
+            classes[{(int)items[i].plan->dtype, items[i].plan->np}].push_back(i);
+        } else {
+            tsmm_status st = tsmm_execute(items[i].plan, items[i].alpha, items[i].A_dev, items[i].lda,
+                                          items[i].pb, items[i].beta, items[i].C_dev, items[i].ldc,
+                                          stream);
+            if (st != TSMM_OK) return st;
+        }
+    }
+    std::unique_ptr<GroupParams> gp(new (std::nothrow) GroupParams());
+    if (!gp) return TSMM_ERR_OUT_OF_MEMORY;
+    for (auto &cls : classes) {
+        const tsmm_dtype dt = (tsmm_dtype)cls.first.first;
+        const int np = cls.first.second;
+        const std::vector<int> &idx = cls.second;
+        for (size_t c0 = 0; c0 < idx.size(); c0 += kGroupMax) {
+            const size_t c1 = std::min(idx.size(), c0 + kGroupMax);
+            int64_t total = 0;
+            int num_sms = 0;
+            gp->count = 0;
+            for (size_t q = c0; q < c1; ++q) {
+                const tsmm_group_item &it = items[idx[q]];
+                tsmm_plan_t p = it.plan;
+                GroupProblem &g = gp->p[gp->count++];
+                const size_t es = dtype_size(dt);
+                const cuuint64_t gdim[2] = {(cuuint64_t)p->m, (cuuint64_t)p->k};
+                const cuuint64_t gstride[1] = {(cuuint64_t)(it.lda * (int64_t)es)};
+                const cuuint32_t box[2] = {(cuuint32_t)p->bm, (cuuint32_t)kTallBKS};
+                const cuuint32_t estr[2] = {1, 1};
+                if (encoder_grouped()(&g.tmA,
+                                      dt == TSMM_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                                     : CU_TENSOR_MAP_DATA_TYPE_FLOAT64,
+                                      2, const_cast<void *>(it.A_dev), gdim, gstride, box, estr,
+                                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+                    return TSMM_ERR_CUDA;
+                TallArgs &a = g.a;
+                a.m = p->m;
+                a.n = p->n;
+                a.k = p->k;
+                a.lda = it.lda;
+                a.ldc = it.ldc;
+                a.A = it.A_dev;
+                a.Bp = it.pb->data;
+                a.C = it.C_dev;
+                a.alpha = it.alpha;
+                a.beta = it.beta;
+                a.ws = p->workspace;
+                a.tickets = p->tickets;
+                a.status = p->status;
+                a.splits = p->splits;
+                a.kchunk = p->kchunk;
+                a.kp = p->kp;
+                a.slabs = p->slabs;
+                g.item_begin = total;
+                total += p->slabs * p->splits;
+                num_sms = p->num_sms;
+            }
+            gp->total_items = total;
+            cudaError_t e = dt == TSMM_F32 ? launch_grouped_f32(np, *gp, num_sms, s)
+                                           : launch_grouped_f64(np, *gp, num_sms, s);
+            if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? TSMM_ERR_OUT_OF_MEMORY : TSMM_ERR_CUDA;
+        }
+    }
+    return TSMM_OK;
+}

@@ -16,7 +16,7 @@ constexpr int kTallBKS = 32;
 // Regime (i): consumer warps per thread block (the producer warp is extra).
 constexpr int kTallConsumerWarps = 4;
 // Regime (ii): packed B tile width (columns) and k granule.
-constexpr int kRankNT = 128;
+constexpr int kRankNT = 64;
 constexpr int kRankKGran = 8;
 constexpr int kRankMaxK = 128;
 constexpr int kTallMaxN = 64;
@@ -32,6 +32,10 @@ inline int tall_np(int64_t n) {
 
 // Rows per thread block of the regime-(i) kernel (see tall kernel header).
 inline int tall_bm(tsmm_dtype d) { return d == TSMM_F64 ? 64 : 128; }
+
+// Thread blocks of the regime-(i) TMA kernel resident per SM (its shared-memory
+// ring is sized for this): 3 for the FMA-bound FP32 shapes (n >= 32), else 2.
+constexpr int tall_resident_blocks(bool f64, int np) { return (!f64 && np >= 32) ? 3 : 2; }
 
 // Regime of a (k, n) pair: 1 = tall (n <= 64), 2 = rank-k (k <= 128), 0 = unsupported.
 inline int regime_of(int64_t k, int64_t n) {
@@ -76,10 +80,13 @@ struct tsmm_plan_s {
     size_t workspace_bytes;
     unsigned *tickets;         // one arrival counter per slab
     unsigned *status;          // device error word
-    // one-entry cache of the TMA descriptor for A
+    // one-entry caches of the TMA descriptors for A and (regime (ii)) C
     const void *tmap_ptr;
     int64_t tmap_lda;
     CUtensorMap tmap;
+    const void *tmapc_ptr;
+    int64_t tmapc_ldc;
+    CUtensorMap tmapc;
 };
 
 namespace tsmm {
@@ -110,11 +117,26 @@ struct RankArgs {
     const void *Bp;  // packed B, ntiles x (kp x kRankNT)
     void *C;
     double alpha, beta;
+    int num_sms;     // persistent grid size = resident blocks x SMs
 };
-cudaError_t launch_rankk(tsmm_dtype dt, const RankArgs &a, cudaStream_t s);
+// tmA: tensor map of A (box bm x 32) or nullptr for the plain-load kernel;
+// tmC: tensor map of C (box bm x kRankNT) when C0 may be prefetched, else nullptr.
+cudaError_t launch_rankk(tsmm_dtype dt, const CUtensorMap *tmA, const CUtensorMap *tmC,
+                         const RankArgs &a, unsigned *status, cudaStream_t s);
 
-// Split-K factor of the regime (i) kernel (planner model in tsmm_api.cu).
-int choose_splits(int64_t slabs, int64_t kstages, int num_sms, int64_t max_splits);
+// Plan construction with an optional forced split count (0 = planner's choice).
+tsmm_status create_plan(int64_t m, int64_t n, int64_t k, tsmm_dtype dtype, int forced_splits,
+                        tsmm_plan_t *out);
+
+// Process-wide plan cache (tsmm_tune.cu): tuned split counts keyed by
+// (dtype, m, n, k, SM count).  Lookup returns 0 when absent.
+int plan_cache_lookup(tsmm_dtype dtype, int64_t m, int64_t n, int64_t k, int sms);
+void plan_cache_store(tsmm_dtype dtype, int64_t m, int64_t n, int64_t k, int sms, int splits);
+
+// Split-K factor of the regime (i) kernel (planner model in tsmm_api.cu);
+// `resident` = thread blocks per SM.
+int choose_splits(int64_t slabs, int64_t kstages, int num_sms, int64_t max_splits,
+                  int resident = 2);
 
 cudaError_t launch_pack_b(tsmm_dtype dt, int64_t k, int64_t n, const void *B, int64_t ldb,
                           void *dst, int64_t kp, int64_t w, int64_t ntiles, cudaStream_t s);

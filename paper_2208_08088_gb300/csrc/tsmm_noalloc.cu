@@ -114,7 +114,8 @@ extern "C" tsmm_status tsmm_execute_noalloc(tsmm_dtype dtype, int64_t m, int64_t
     const int64_t room = (int64_t)(kScratchBytes - off_ws);
     int64_t max_splits = std::min<int64_t>(65535, per_split > 0 ? room / per_split : 1);
     if (max_splits < 2) max_splits = 1;
-    const int splits_req = choose_splits(slabs, kstages, sms, max_splits);
+    const int splits_req =
+        choose_splits(slabs, kstages, sms, max_splits, tall_resident_blocks(dtype == TSMM_F64, np));
     const int64_t chunk_stages = (kstages + splits_req - 1) / splits_req;
     const int splits = (int)((kstages + chunk_stages - 1) / chunk_stages);
 

@@ -4,12 +4,20 @@
 // contracted on chip, so the kernel streams C0 in and C out exactly once:
 // the traffic floor of this shape is the 2*m*n output read/write, not A or B.
 //
-// Thread block: 256 threads own a BMT x 128 tile of C.  Each thread keeps a
-// (2*VEC) x 8 register tile split in two row groups {tm*VEC + r} and
-// {BMT/2 + tm*VEC + r} and two column groups {tn*4 + c} and {64 + tn*4 + c}, so
-// that both the shared-memory operand reads and the global C0 loads / C stores
-// of a half-warp cover one contiguous 256-byte run.  k is consumed in chunks of
-// KC = 32 staged through shared memory.
+// Thread block: 256 consumer threads own a BMT x 64 tile of C.  Each thread
+// keeps a (2*VEC) x 4 register tile: two row groups {tm*VEC + r} and
+// {BMT/2 + tm*VEC + r} (one 16-byte vector each) and the columns {tn*4 + c},
+// so that both the shared-memory operand reads and the global C stores of a
+// half-warp cover one contiguous 256-byte run.
+//
+// TMA path (A 16-byte aligned with lda*s a multiple of 16): one producer warp
+// streams k in chunks of KC = 32 -- a 2-D tensor copy of A (BMT x KC) and a
+// bulk copy of the packed B rows (KC x 64) per chunk -- through a ring of
+// STAGES mbarrier-guarded buffers.  For the output-bound small-k shapes
+// (PREFETCH_C0) it also fetches the whole C0 tile with one tensor copy at block
+// start, so the C0 read overlaps the A/B traffic and the products; otherwise
+// the epilogue loads C0 in batches ahead of its stores.  A plain-load kernel
+// covers unaligned A.
 #include "tsmm_device.cuh"
 #include "tsmm_internal.h"
 
@@ -19,17 +27,295 @@ template <typename T>
 struct RankCfg {
     static constexpr int VEC = 16 / (int)sizeof(T);
     static constexpr int TM = 2 * VEC;         // rows per thread (two row groups)
-    static constexpr int TN = 8;               // columns per thread (two column groups)
+    static constexpr int TN = 4;               // columns per thread
     static constexpr int BMT = 16 * TM;        // 128 (f32) / 64 (f64)
-    static constexpr int BNT = kRankNT;        // 128
+    static constexpr int BNT = kRankNT;        // 64
     static constexpr int KC = 32;
-    static constexpr int THREADS = 256;
-    static constexpr int SMEM = KC * (BMT + BNT) * (int)sizeof(T);
+    static constexpr int CONSUMERS = 256;
+    static constexpr int A_CHUNK = BMT * KC;   // elements
+    static constexpr int B_CHUNK = KC * BNT;
+    static constexpr int C_TILE = BMT * BNT;
     static_assert(BNT == 16 * TN, "tile width");
 };
 
+// Register tile of one thread: rows {rg*BMT/2 + tm*VEC + r} (rg = 0, 1;
+// r < VEC) x columns {tn*4 + c} (c < 4); row index R = rg*VEC + r.  Each
+// product is an IEEE fma in the working precision.  The FP32 tile keeps row
+// pairs as float2 and uses the packed FP32x2 fma (same roundings as two scalar
+// fmas, half the issue slots), with each B value duplicated into both halves.
 template <typename T>
-__global__ void __launch_bounds__(256, 2) rankk_kernel(const RankArgs a, bool vec_a, bool vec_c) {
+struct RankAcc {
+    using Cfg = RankCfg<T>;
+    T v[Cfg::TM][Cfg::TN];
+    __device__ __forceinline__ void zero() {
+#pragma unroll
+        for (int r = 0; r < Cfg::TM; ++r)
+#pragma unroll
+            for (int c = 0; c < Cfg::TN; ++c) v[r][c] = T(0);
+    }
+    // one k-chunk from shared memory (As: [KC][BMT], Bs: [KC][BNT])
+    __device__ __forceinline__ void chunk(const T *As, const T *Bs, int kcnt, int tm, int tn) {
+        constexpr int V = Cfg::VEC;
+#pragma unroll 4
+        for (int pc = 0; pc < kcnt; ++pc) {
+            const Vec<T, V> a0 = ld_vec<T, V>(As + pc * Cfg::BMT + tm * V);
+            const Vec<T, V> a1 = ld_vec<T, V>(As + pc * Cfg::BMT + Cfg::BMT / 2 + tm * V);
+            const Vec<T, 4> b0 = *reinterpret_cast<const Vec<T, 4> *>(Bs + pc * Cfg::BNT + tn * 4);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+#pragma unroll
+                for (int r = 0; r < V; ++r) {
+                    v[r][c] = fma(a0.v[r], b0.v[c], v[r][c]);
+                    v[V + r][c] = fma(a1.v[r], b0.v[c], v[V + r][c]);
+                }
+            }
+        }
+    }
+    __device__ __forceinline__ T get(int r, int c) const { return v[r][c]; }
+};
+
+template <>
+struct RankAcc<float> {
+    using Cfg = RankCfg<float>;
+    float2 v[Cfg::TM / 2][Cfg::TN];
+    __device__ __forceinline__ void zero() {
+#pragma unroll
+        for (int r = 0; r < Cfg::TM / 2; ++r)
+#pragma unroll
+            for (int c = 0; c < Cfg::TN; ++c) v[r][c] = make_float2(0.f, 0.f);
+    }
+    __device__ __forceinline__ void chunk(const float *As, const float *Bs, int kcnt, int tm, int tn) {
+#pragma unroll 4
+        for (int pc = 0; pc < kcnt; ++pc) {
+            const float4 a0 = *reinterpret_cast<const float4 *>(As + pc * Cfg::BMT + tm * 4);
+            const float4 a1 = *reinterpret_cast<const float4 *>(As + pc * Cfg::BMT + Cfg::BMT / 2 + tm * 4);
+            const float4 b = *reinterpret_cast<const float4 *>(Bs + pc * Cfg::BNT + tn * 4);
+            const float2 ap[4] = {make_float2(a0.x, a0.y), make_float2(a0.z, a0.w),
+                                  make_float2(a1.x, a1.y), make_float2(a1.z, a1.w)};
+            const float2 bd[4] = {make_float2(b.x, b.x), make_float2(b.y, b.y),
+                                  make_float2(b.z, b.z), make_float2(b.w, b.w)};
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+#pragma unroll
+                for (int rp = 0; rp < 4; ++rp) v[rp][c] = __ffma2_rn(ap[rp], bd[c], v[rp][c]);
+        }
+    }
+    __device__ __forceinline__ float get(int r, int c) const {
+        return (r & 1) ? v[r / 2][c].y : v[r / 2][c].x;
+    }
+};
+
+// Epilogue C = alpha*acc + beta*C0 in two phases so that C0 can come from a
+// shared-memory buffer that is released between them.  Phase 1 gathers this
+// thread's C0 values -- from the tile sC ([BNT][BMT], as the tensor copy lays it
+// out) when given, else from global memory, all loads ahead of any store so
+// they do not wait behind stores to the same array; phase 2 stores.
+template <typename T>
+struct RankEpilogue {
+    using Cfg = RankCfg<T>;
+    static constexpr int V = Cfg::VEC;
+    Vec<T, V> c0v[4][2];
+
+    __device__ __forceinline__ void load(const RankArgs &a, int64_t i0, int64_t tile, int tm, int tn,
+                                         bool vec_c, const T *sC) {
+        const T beta = static_cast<T>(a.beta);
+        const T *C = static_cast<const T *>(a.C);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int jl = tn * 4 + c;
+            const int64_t j = tile * Cfg::BNT + jl;
+#pragma unroll
+            for (int rg = 0; rg < 2; ++rg) {
+                const int il = rg * (Cfg::BMT / 2) + tm * V;
+                const int64_t i = i0 + il;
+#pragma unroll
+                for (int r = 0; r < V; ++r) c0v[c][rg].v[r] = T(0);
+                if (beta == T(0) || j >= a.n) continue;
+                if (sC) {
+                    c0v[c][rg] = ld_vec<T, V>(sC + jl * Cfg::BMT + il);
+                } else if (vec_c && i + V <= a.m) {
+                    c0v[c][rg] = ld_vec<T, V>(C + i + j * a.ldc);
+                } else {
+#pragma unroll
+                    for (int r = 0; r < V; ++r)
+                        if (i + r < a.m) c0v[c][rg].v[r] = C[i + r + j * a.ldc];
+                }
+            }
+        }
+    }
+
+    __device__ __forceinline__ void store(const RankAcc<T> &acc, const RankArgs &a, int64_t i0,
+                                          int64_t tile, int tm, int tn, bool vec_c) const {
+        const T alpha = static_cast<T>(a.alpha);
+        const T beta = static_cast<T>(a.beta);
+        T *C = static_cast<T *>(a.C);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int64_t j = tile * Cfg::BNT + tn * 4 + c;
+            if (j >= a.n) continue;
+#pragma unroll
+            for (int rg = 0; rg < 2; ++rg) {
+                const int64_t i = i0 + rg * (Cfg::BMT / 2) + tm * V;
+                Vec<T, V> o;
+#pragma unroll
+                for (int r = 0; r < V; ++r) {
+                    const T x = acc.get(rg * V + r, c);
+                    o.v[r] = (alpha == T(1)) ? x : alpha * x;  // alpha*x == x exactly when alpha is 1
+                    if (beta != T(0)) o.v[r] = fma(beta, c0v[c][rg].v[r], o.v[r]);
+                }
+                T *cp = C + i + j * a.ldc;
+                if (vec_c && i + V <= a.m) {
+                    st_vec<T, V>(cp, o);
+                } else {
+#pragma unroll
+                    for (int r = 0; r < V; ++r)
+                        if (i + r < a.m) cp[r] = o.v[r];
+                }
+            }
+        }
+    }
+};
+
+template <typename T, int STAGES, bool PREFETCH_C0>
+struct RankTmaCfg {
+    using Cfg = RankCfg<T>;
+    static constexpr int STAGE_ELEMS = Cfg::A_CHUNK + Cfg::B_CHUNK;
+    static constexpr int CBUF = PREFETCH_C0 ? 2 : 0;   // double-buffered C0 tiles
+    static constexpr int DATA_BYTES = (STAGES * STAGE_ELEMS + CBUF * Cfg::C_TILE) * (int)sizeof(T);
+    static constexpr int NBAR = 2 * STAGES + 2 * CBUF;
+    static constexpr int SMEM = DATA_BYTES + NBAR * 8 + 16;
+    static constexpr int THREADS = Cfg::CONSUMERS + 32;
+    static constexpr int RESIDENT = 2;                  // blocks per SM (registers, shared memory)
+};
+
+// Persistent: each block walks tiles t = blockIdx.x, blockIdx.x + gridDim.x, ...
+// (tile t covers rows (t % mtiles)*BMT and columns (t / mtiles)*BNT).  The
+// producer warp runs ahead of the consumers by up to STAGES k-chunks and, with
+// PREFETCH_C0, by one C0 tile, so the next tile's loads overlap this tile's
+// products and stores.
+template <typename T, int STAGES, bool PREFETCH_C0>
+__global__ void __launch_bounds__(RankCfg<T>::CONSUMERS + 32, 2)
+    rankk_tma_kernel(const __grid_constant__ CUtensorMap tmA,
+                     const __grid_constant__ CUtensorMap tmC, const RankArgs a, bool vec_c,
+                     unsigned *status) {
+    using Cfg = RankCfg<T>;
+    using TC = RankTmaCfg<T, STAGES, PREFETCH_C0>;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    T *sStage = reinterpret_cast<T *>(smem_raw);
+    T *sC = sStage + STAGES * TC::STAGE_ELEMS;
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem_raw + TC::DATA_BYTES);
+    uint64_t *empty = full + STAGES;
+    uint64_t *cfull = empty + STAGES;  // CBUF entries
+    uint64_t *cempty = cfull + TC::CBUF;
+
+    const int warp = threadIdx.x / 32;
+    const int lane = threadIdx.x % 32;
+    const int64_t mtiles = (a.m + Cfg::BMT - 1) / Cfg::BMT;
+    const int64_t ntiles_total = mtiles * ((a.n + Cfg::BNT - 1) / Cfg::BNT);
+    const int nchunks = (int)((a.k + Cfg::KC - 1) / Cfg::KC);
+    const bool want_c0 = PREFETCH_C0 && a.beta != 0.0;
+
+    if (threadIdx.x == 0) {
+        prefetch_tmap(&tmA);
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], Cfg::CONSUMERS / 32);
+        }
+        for (int b = 0; b < TC::CBUF; ++b) {
+            mbar_init(&cfull[b], 1);
+            mbar_init(&cempty[b], Cfg::CONSUMERS / 32);
+        }
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    if (warp == Cfg::CONSUMERS / 32) {
+        if (lane == 0) {
+            const uint64_t pol_stream = policy_evict_first();
+            const uint64_t pol_keep = policy_evict_last();
+            int64_t g = 0;  // k-chunks issued so far by this block
+            int j = 0;      // tiles issued so far by this block
+            bool ok = true;
+            for (int64_t t = blockIdx.x; t < ntiles_total && ok; t += gridDim.x, ++j) {
+                const int64_t i0 = (t % mtiles) * Cfg::BMT;
+                const int64_t tile = t / mtiles;
+                if (want_c0) {
+                    const int b = j % 2;
+                    if (j >= 2 && !mbar_wait_bounded(&cempty[b], ((j / 2) & 1) ^ 1)) {
+                        ok = false;
+                        break;
+                    }
+                    T *dst = sC + b * Cfg::C_TILE;
+                    mbar_arrive_expect_tx(&cfull[b], Cfg::C_TILE * (int)sizeof(T));
+                    tma_load_2d(dst, &tmC, (int32_t)i0, (int32_t)(tile * Cfg::BNT), &cfull[b],
+                                pol_stream);
+                }
+                const T *Bt = static_cast<const T *>(a.Bp) + tile * a.kp * Cfg::BNT;
+                for (int c = 0; c < nchunks; ++c, ++g) {
+                    const int st = (int)(g % STAGES);
+                    if (g >= STAGES && !mbar_wait_bounded(&empty[st], (int)((g / STAGES) & 1) ^ 1)) {
+                        ok = false;
+                        break;
+                    }
+                    const int64_t kc = (int64_t)c * Cfg::KC;
+                    const int brows = (int)((a.kp - kc < Cfg::KC) ? a.kp - kc : Cfg::KC);
+                    T *sA = sStage + st * TC::STAGE_ELEMS;
+                    T *sB = sA + Cfg::A_CHUNK;
+                    mbar_arrive_expect_tx(&full[st],
+                                          (Cfg::A_CHUNK + brows * Cfg::BNT) * (int)sizeof(T));
+                    tma_load_2d(sA, &tmA, (int32_t)i0, (int32_t)kc, &full[st], pol_keep);
+                    bulk_load(sB, Bt + kc * Cfg::BNT, brows * Cfg::BNT * (int)sizeof(T), &full[st],
+                              pol_keep);
+                }
+            }
+            if (!ok) atomicOr(status, kDevErrTimeout);
+        }
+        return;
+    }
+
+    const int tid = threadIdx.x;
+    const int tm = tid % 16;
+    const int tn = tid / 16;
+    int64_t g = 0;
+    int j = 0;
+    for (int64_t t = blockIdx.x; t < ntiles_total; t += gridDim.x, ++j) {
+        const int64_t i0 = (t % mtiles) * Cfg::BMT;
+        const int64_t tile = t / mtiles;
+        RankAcc<T> acc;
+        acc.zero();
+        bool ok = true;
+        for (int c = 0; c < nchunks; ++c, ++g) {
+            const int st = (int)(g % STAGES);
+            if (!mbar_wait_bounded(&full[st], (int)((g / STAGES) & 1))) {
+                ok = false;
+                break;
+            }
+            const int64_t kc = (int64_t)c * Cfg::KC;
+            const int kcnt = (int)((a.k - kc < Cfg::KC) ? a.k - kc : Cfg::KC);
+            const T *sA = sStage + st * TC::STAGE_ELEMS;
+            acc.chunk(sA, sA + Cfg::A_CHUNK, kcnt, tm, tn);
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[st]);
+        }
+        RankEpilogue<T> ep;
+        const int b = j % 2;
+        if (ok && want_c0 && !mbar_wait_bounded(&cfull[b], (j / 2) & 1)) ok = false;
+        if (!ok) {
+            if (lane == 0) atomicOr(status, kDevErrTimeout);
+            return;  // this warp's part of the tile is not written; the host sees TSMM_ERR_TIMEOUT
+        }
+        ep.load(a, i0, tile, tm, tn, vec_c, want_c0 ? sC + b * Cfg::C_TILE : nullptr);
+        if (want_c0) {
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&cempty[b]);  // C0 buffer b may be refilled
+        }
+        ep.store(acc, a, i0, tile, tm, tn, vec_c);
+    }
+}
+
+// Plain-load kernel for an A that a tensor map cannot describe.
+template <typename T>
+__global__ void __launch_bounds__(256, 2) rankk_plain_kernel(const RankArgs a, bool vec_a, bool vec_c) {
     using Cfg = RankCfg<T>;
     constexpr int V = Cfg::VEC;
     constexpr int BMT = Cfg::BMT;
@@ -47,15 +333,11 @@ __global__ void __launch_bounds__(256, 2) rankk_kernel(const RankArgs a, bool ve
     const T *A = static_cast<const T *>(a.A);
     const T *Bt = static_cast<const T *>(a.Bp) + tile * a.kp * BNT;
 
-    T acc[Cfg::TM][Cfg::TN];
-#pragma unroll
-    for (int r = 0; r < Cfg::TM; ++r)
-#pragma unroll
-        for (int c = 0; c < Cfg::TN; ++c) acc[r][c] = T(0);
+    RankAcc<T> acc;
+    acc.zero();
 
     for (int64_t kc = 0; kc < a.k; kc += KC) {
-        // ---- stage A[i0 .. i0+BMT) x [kc .. kc+KC) as As[p][i]
-        for (int e = tid * V; e < KC * BMT; e += Cfg::THREADS * V) {
+        for (int e = tid * V; e < KC * BMT; e += Cfg::CONSUMERS * V) {
             const int pc = e / BMT;
             const int il = e % BMT;
             const int64_t p = kc + pc;
@@ -70,10 +352,8 @@ __global__ void __launch_bounds__(256, 2) rankk_kernel(const RankArgs a, bool ve
             }
             st_vec<T, V>(As + e, v);
         }
-        // ---- stage packed B rows [kc .. kc+KC) of this column tile as Bs[p][j]
-        for (int e = tid * V; e < KC * BNT; e += Cfg::THREADS * V) {
-            const int pc = e / BNT;
-            const int64_t p = kc + pc;
+        for (int e = tid * V; e < KC * BNT; e += Cfg::CONSUMERS * V) {
+            const int64_t p = kc + e / BNT;
             Vec<T, V> v;
             if (p < a.kp) {
                 v = ld_vec<T, V>(Bt + p * BNT + (e % BNT));
@@ -85,79 +365,60 @@ __global__ void __launch_bounds__(256, 2) rankk_kernel(const RankArgs a, bool ve
         }
         __syncthreads();
         const int kcnt = (a.k - kc < KC) ? (int)(a.k - kc) : KC;
-#pragma unroll 4
-        for (int pc = 0; pc < kcnt; ++pc) {
-            const Vec<T, V> a0 = ld_vec<T, V>(As + pc * BMT + tm * V);
-            const Vec<T, V> a1 = ld_vec<T, V>(As + pc * BMT + BMT / 2 + tm * V);
-            const Vec<T, 4> b0 = *reinterpret_cast<const Vec<T, 4> *>(Bs + pc * BNT + tn * 4);
-            const Vec<T, 4> b1 = *reinterpret_cast<const Vec<T, 4> *>(Bs + pc * BNT + 64 + tn * 4);
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-#pragma unroll
-                for (int r = 0; r < V; ++r) {
-                    acc[r][c] = fma(a0.v[r], b0.v[c], acc[r][c]);
-                    acc[V + r][c] = fma(a1.v[r], b0.v[c], acc[V + r][c]);
-                    acc[r][4 + c] = fma(a0.v[r], b1.v[c], acc[r][4 + c]);
-                    acc[V + r][4 + c] = fma(a1.v[r], b1.v[c], acc[V + r][4 + c]);
-                }
-            }
-        }
+        acc.chunk(As, Bs, kcnt, tm, tn);
         __syncthreads();
     }
+    RankEpilogue<T> ep;
+    ep.load(a, i0, tile, tm, tn, vec_c, nullptr);
+    ep.store(acc, a, i0, tile, tm, tn, vec_c);
+}
 
-    // ---- epilogue: C = alpha*acc + beta*C0, one pass over the tile
-    const T alpha = static_cast<T>(a.alpha);
-    const T beta = static_cast<T>(a.beta);
-    T *C = static_cast<T *>(a.C);
-#pragma unroll
-    for (int cg = 0; cg < 2; ++cg) {
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            const int64_t j = tile * BNT + cg * 64 + tn * 4 + c;
-            if (j >= a.n) continue;
-#pragma unroll
-            for (int rg = 0; rg < 2; ++rg) {
-                const int64_t i = i0 + rg * (BMT / 2) + tm * V;
-                T *cp = C + i + j * a.ldc;
-                if (vec_c && i + V <= a.m) {
-                    Vec<T, V> o;
-#pragma unroll
-                    for (int r = 0; r < V; ++r) o.v[r] = alpha * acc[rg * V + r][cg * 4 + c];
-                    if (beta != T(0)) {
-                        const Vec<T, V> c0 = ld_vec<T, V>(cp);
-#pragma unroll
-                        for (int r = 0; r < V; ++r) o.v[r] = fma(beta, c0.v[r], o.v[r]);
-                    }
-                    st_vec<T, V>(cp, o);
-                } else {
-#pragma unroll
-                    for (int r = 0; r < V; ++r) {
-                        if (i + r < a.m) {
-                            T o = alpha * acc[rg * V + r][cg * 4 + c];
-                            if (beta != T(0)) o = fma(beta, cp[r], o);
-                            cp[r] = o;
-                        }
-                    }
-                }
-            }
-        }
+template <typename T, int STAGES, bool PF>
+static cudaError_t launch_rankk_tma_t(const CUtensorMap *tmA, const CUtensorMap *tmC,
+                                      const RankArgs &a, bool vec_c, unsigned *status,
+                                      cudaStream_t s) {
+    using Cfg = RankCfg<T>;
+    using TC = RankTmaCfg<T, STAGES, PF>;
+    static bool attr_done = false;
+    if (!attr_done) {
+        cudaError_t e = cudaFuncSetAttribute(rankk_tma_kernel<T, STAGES, PF>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, TC::SMEM);
+        if (e != cudaSuccess) return e;
+        attr_done = true;
     }
+    const int64_t tiles = ((a.m + Cfg::BMT - 1) / Cfg::BMT) * ((a.n + Cfg::BNT - 1) / Cfg::BNT);
+    const int64_t slots = (int64_t)TC::RESIDENT * (a.num_sms > 0 ? a.num_sms : 1);
+    const unsigned grid = (unsigned)(tiles < slots ? tiles : slots);
+    rankk_tma_kernel<T, STAGES, PF><<<grid, TC::THREADS, TC::SMEM, s>>>(*tmA, *tmC, a, vec_c, status);
+    return cudaGetLastError();
 }
 
 template <typename T>
-static cudaError_t launch_rankk_t(const RankArgs &a, cudaStream_t s) {
+static cudaError_t launch_rankk_t(const CUtensorMap *tmA, const CUtensorMap *tmC, const RankArgs &a,
+                                  unsigned *status, cudaStream_t s) {
     using Cfg = RankCfg<T>;
     const bool vec_a = (reinterpret_cast<uintptr_t>(a.A) % 16 == 0) &&
                        ((a.lda * (int64_t)sizeof(T)) % 16 == 0);
     const bool vec_c = (reinterpret_cast<uintptr_t>(a.C) % 16 == 0) &&
                        ((a.ldc * (int64_t)sizeof(T)) % 16 == 0);
+    if (tmA) {
+        // output-bound shapes: one k chunk, C0 prefetched by TMA when it is read
+        if (a.k <= Cfg::KC) {
+            if (tmC && a.beta != 0.0) return launch_rankk_tma_t<T, 1, true>(tmA, tmC, a, vec_c, status, s);
+            return launch_rankk_tma_t<T, 1, false>(tmA, tmA, a, vec_c, status, s);
+        }
+        return launch_rankk_tma_t<T, 2, false>(tmA, tmA, a, vec_c, status, s);
+    }
+    const int smem = Cfg::KC * (Cfg::BMT + Cfg::BNT) * (int)sizeof(T);
     dim3 grid((unsigned)((a.m + Cfg::BMT - 1) / Cfg::BMT), (unsigned)((a.n + Cfg::BNT - 1) / Cfg::BNT));
-    rankk_kernel<T><<<grid, Cfg::THREADS, Cfg::SMEM, s>>>(a, vec_a, vec_c);
+    rankk_plain_kernel<T><<<grid, Cfg::CONSUMERS, smem, s>>>(a, vec_a, vec_c);
     return cudaGetLastError();
 }
 
-cudaError_t launch_rankk(tsmm_dtype dt, const RankArgs &a, cudaStream_t s) {
-    return dt == TSMM_F32 ? launch_rankk_t<float>(a, s) : launch_rankk_t<double>(a, s);
+cudaError_t launch_rankk(tsmm_dtype dt, const CUtensorMap *tmA, const CUtensorMap *tmC,
+                         const RankArgs &a, unsigned *status, cudaStream_t s) {
+    return dt == TSMM_F32 ? launch_rankk_t<float>(tmA, tmC, a, status, s)
+                          : launch_rankk_t<double>(tmA, tmC, a, status, s);
 }
 
 }  // namespace tsmm

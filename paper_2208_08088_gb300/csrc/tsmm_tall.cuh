@@ -23,6 +23,8 @@
 // in shared memory in warp order, then either stored (one split) or written to
 // the split-K workspace and finished by the last-arriving block.
 #pragma once
+#include <type_traits>
+
 #include "tsmm_device.cuh"
 #include "tsmm_internal.h"
 
@@ -46,7 +48,12 @@ struct TallCfg {
     static constexpr int A_STAGE = BM * BKS;           // elements
     static constexpr int B_STAGE = BKS * NP;           // elements
     static constexpr int STAGE_BYTES = (A_STAGE + B_STAGE) * (int)sizeof(T);
-    static constexpr int STAGES_RAW = (100 * 1024) / STAGE_BYTES;
+    // Resident blocks per SM the ring is sized for: FMA-bound shapes (FP32,
+    // n >= 32) want more warps to hide shared-memory latency and need less data
+    // in flight, so they get a shorter ring and three blocks per SM.
+    static constexpr int RESIDENT = tall_resident_blocks(sizeof(T) == 8, NP);
+    static constexpr int SMEM_BUDGET = RESIDENT >= 3 ? 72 * 1024 : 100 * 1024;
+    static constexpr int STAGES_RAW = SMEM_BUDGET / STAGE_BYTES;
     static constexpr int STAGES = STAGES_RAW < 2 ? 2 : (STAGES_RAW > 6 ? 6 : STAGES_RAW);
     static constexpr int RED = WK * NP * BM;           // reduction buffer elements
     static constexpr int DATA_BYTES = STAGES * STAGE_BYTES > RED * (int)sizeof(T)
@@ -152,24 +159,79 @@ __device__ __forceinline__ void tall_finish(T *red, const TallArgs &a, int64_t s
     if (ctid == 0) a.tickets[slab] = 0u;  // ready for the next launch on this stream
 }
 
-// Accumulate one A column (R rows, vector) against NP packed B values.
-template <typename T, int NP>
-__device__ __forceinline__ void tall_fma_column(T (&acc)[TallCfg<T, NP>::R][TallCfg<T, NP>::CN],
-                                                const Vec<T, TallCfg<T, NP>::R> &av,
-                                                const T *bsrc) {
-    using Cfg = TallCfg<T, NP>;
+// Register tile of one thread: R rows x CN columns of C.  acc(r, c) +=
+// A[r] * B[c] for one A column at a time, each product an IEEE fma in the
+// working precision.  FP32 tiles with CN >= 2 store column pairs as float2 and
+// use the packed FP32x2 fma (fma.rn.f32x2): the same two roundings as two
+// scalar fmas, in half the issue slots, which leaves room for the shared-
+// memory loads of A and B in the FMA-bound cases (n >= 16).
+template <typename T, int R, int CN, int BV>
+struct AccTile {
+    T v[R][CN];
+    __device__ __forceinline__ void zero() {
 #pragma unroll
-    for (int c0 = 0; c0 < Cfg::CN; c0 += Cfg::BV) {
-        const Vec<T, Cfg::BV> bv = ld_vec<T, Cfg::BV>(bsrc + c0);
+        for (int r = 0; r < R; ++r)
 #pragma unroll
-        for (int c = 0; c < Cfg::BV; ++c)
-#pragma unroll
-            for (int r = 0; r < Cfg::R; ++r) acc[r][c0 + c] = fma(av.v[r], bv.v[c], acc[r][c0 + c]);
+            for (int c = 0; c < CN; ++c) v[r][c] = T(0);
     }
-}
+    __device__ __forceinline__ void fma_column(const Vec<T, R> &av, const T *bsrc) {
+#pragma unroll
+        for (int c0 = 0; c0 < CN; c0 += BV) {
+            const Vec<T, BV> bv = ld_vec<T, BV>(bsrc + c0);
+#pragma unroll
+            for (int c = 0; c < BV; ++c)
+#pragma unroll
+                for (int r = 0; r < R; ++r) v[r][c0 + c] = fma(av.v[r], bv.v[c], v[r][c0 + c]);
+        }
+    }
+    __device__ __forceinline__ T get(int r, int c) const { return v[r][c]; }
+};
+
+template <int R, int CN>
+struct AccTilePairs {
+    float2 v[R][CN / 2];
+    __device__ __forceinline__ void zero() {
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+#pragma unroll
+            for (int c = 0; c < CN / 2; ++c) v[r][c] = make_float2(0.f, 0.f);
+    }
+    __device__ __forceinline__ void fma_column(const Vec<float, R> &av, const float *bsrc) {
+        float2 ad[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) ad[r] = make_float2(av.v[r], av.v[r]);
+        constexpr int BV = CN < 4 ? CN : 4;
+#pragma unroll
+        for (int c0 = 0; c0 < CN; c0 += BV) {
+            const Vec<float, BV> bv = ld_vec<float, BV>(bsrc + c0);
+#pragma unroll
+            for (int c = 0; c < BV; c += 2) {
+                const float2 b2 = make_float2(bv.v[c], bv.v[c + 1]);
+#pragma unroll
+                for (int r = 0; r < R; ++r)
+                    v[r][(c0 + c) / 2] = __ffma2_rn(ad[r], b2, v[r][(c0 + c) / 2]);
+            }
+        }
+    }
+    __device__ __forceinline__ float get(int r, int c) const {
+        return (c & 1) ? v[r][c / 2].y : v[r][c / 2].x;
+    }
+};
 
 template <typename T, int NP>
-__global__ void __launch_bounds__(TallCfg<T, NP>::THREADS, 2)
+struct TallAcc {
+    using Cfg = TallCfg<T, NP>;
+    using type = AccTile<T, Cfg::R, Cfg::CN, Cfg::BV>;
+};
+template <int NP>
+struct TallAcc<float, NP> {
+    using Cfg = TallCfg<float, NP>;
+    using type = typename std::conditional<(Cfg::CN >= 2), AccTilePairs<Cfg::R, Cfg::CN>,
+                                           AccTile<float, Cfg::R, Cfg::CN, Cfg::BV>>::type;
+};
+
+template <typename T, int NP>
+__global__ void __launch_bounds__(TallCfg<T, NP>::THREADS, TallCfg<T, NP>::RESIDENT)
     tall_tma_kernel(const __grid_constant__ CUtensorMap tmA, const TallArgs a) {
     using Cfg = TallCfg<T, NP>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -232,11 +294,8 @@ __global__ void __launch_bounds__(TallCfg<T, NP>::THREADS, 2)
     const int rloc = wm * Cfg::WROWS + lr * Cfg::R;  // first local row of this thread
     const int cloc = g * Cfg::CN;                    // first column of this thread
 
-    T acc[Cfg::R][Cfg::CN];
-#pragma unroll
-    for (int r = 0; r < Cfg::R; ++r)
-#pragma unroll
-        for (int c = 0; c < Cfg::CN; ++c) acc[r][c] = T(0);
+    typename TallAcc<T, NP>::type acc;
+    acc.zero();
 
     bool ok = true;
     for (int it = 0; it < iters; ++it) {
@@ -251,7 +310,7 @@ __global__ void __launch_bounds__(TallCfg<T, NP>::THREADS, 2)
         for (int c = 0; c < Cfg::KPW; ++c) {
             const int col = wk * Cfg::KPW + c;
             const Vec<T, Cfg::R> av = ld_vec<T, Cfg::R>(As + col * Cfg::BM + rloc);
-            tall_fma_column<T, NP>(acc, av, Bs + col * NP + cloc);
+            acc.fma_column(av, Bs + col * NP + cloc);
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[st]);
@@ -270,7 +329,7 @@ __global__ void __launch_bounds__(TallCfg<T, NP>::THREADS, 2)
     for (int c = 0; c < Cfg::CN; ++c) {
         Vec<T, Cfg::R> v;
 #pragma unroll
-        for (int r = 0; r < Cfg::R; ++r) v.v[r] = acc[r][c];
+        for (int r = 0; r < Cfg::R; ++r) v.v[r] = acc.get(r, c);
         st_vec<T, Cfg::R>(red + (wk * NP + cloc + c) * Cfg::BM + rloc, v);
     }
     named_barrier(1, Cfg::CONSUMERS);
@@ -303,11 +362,8 @@ __global__ void __launch_bounds__(TallCfg<T, NP>::CONSUMERS, 2)
     const T *A = static_cast<const T *>(a.A);
     const T *Bp = static_cast<const T *>(a.Bp);
 
-    T acc[Cfg::R][Cfg::CN];
-#pragma unroll
-    for (int r = 0; r < Cfg::R; ++r)
-#pragma unroll
-        for (int c = 0; c < Cfg::CN; ++c) acc[r][c] = T(0);
+    typename TallAcc<T, NP>::type acc;
+    acc.zero();
 
     for (int64_t kb = k0; kb < k1; kb += Cfg::BKS) {
         for (int c = 0; c < Cfg::KPW; ++c) {
@@ -317,14 +373,14 @@ __global__ void __launch_bounds__(TallCfg<T, NP>::CONSUMERS, 2)
 #pragma unroll
             for (int r = 0; r < Cfg::R; ++r)
                 av.v[r] = (i0 + r < a.m) ? A[i0 + r + p * a.lda] : T(0);
-            tall_fma_column<T, NP>(acc, av, Bp + p * NP + cloc);
+            acc.fma_column(av, Bp + p * NP + cloc);
         }
     }
 #pragma unroll
     for (int c = 0; c < Cfg::CN; ++c) {
         Vec<T, Cfg::R> v;
 #pragma unroll
-        for (int r = 0; r < Cfg::R; ++r) v.v[r] = acc[r][c];
+        for (int r = 0; r < Cfg::R; ++r) v.v[r] = acc.get(r, c);
         st_vec<T, Cfg::R>(red + (wk * NP + cloc + c) * Cfg::BM + rloc, v);
     }
     named_barrier(1, Cfg::CONSUMERS);

@@ -251,3 +251,16 @@ def test_plan_reuse_across_A_pointers():
     for A in (A1, A2, A1):
         C, _, _ = run(A, B, C0, 1.0, 0.0, plan=pl, pb=pb)
         assert_parity(C, A, B, None, 1.0, 0.0)
+
+
+@pytest.mark.parametrize("dtype", DT)
+@pytest.mark.parametrize("k", [3, 16, 32, 33, 100])
+@pytest.mark.parametrize("beta", [0.0, 1.0, -0.5])
+def test_rankk_persistent_many_tiles(dtype, k, beta):
+    """More tiles than resident blocks: every block walks several tiles, reusing
+    its k-chunk ring and (k <= 32, beta != 0) its two C0 buffers."""
+    m, n = 2050, 1000
+    A, B, C0 = gen(m, n, k, dtype)
+    C, pl, _ = run(A, B, C0 if beta != 0 else None, 1.0 if k != 33 else 0.75, beta)
+    assert pl.info()["regime"] == 2
+    assert_parity(C, A, B, C0 if beta != 0 else None, 1.0 if k != 33 else 0.75, beta)

@@ -265,19 +265,26 @@ def run_reference(args):
 
 
 # --------------------------------------------------------------------- our arm
-def kernel_source_hash():
+KERNEL_SOURCES = {  # the files that define each kernel family's device code
+    "tall": ["tsmm_tall.cuh", "tsmm_device.cuh"],
+    "rankk": ["tsmm_rankk.cu", "tsmm_device.cuh"],
+}
+
+
+def kernel_source_hash(family):
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2208_08088_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
+    for name in KERNEL_SOURCES[family]:
         with open(os.path.join(csrc, name), "rb") as f:
             h.update(name.encode())
             h.update(f.read())
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(kernel_key):
-    """DRAM bytes per launch from a committed ncu summary, if it was taken on
-    the current kernel sources; else None."""
+def recorded_traffic(kernel_key, family):
+    """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum)
+    from the committed ncu record, if it was taken on the current sources of
+    this kernel family; else None."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
@@ -285,7 +292,7 @@ def recorded_traffic(kernel_key):
     except Exception:
         return None
     ent = d.get(kernel_key)
-    if not ent or ent.get("source_hash") != kernel_source_hash():
+    if not ent or ent.get("source_hash") != kernel_source_hash(family):
         return None
     return ent.get("dram_bytes_per_launch")
 
@@ -407,7 +414,7 @@ def run_ours(args):
                 "unit": "TFLOP/s", "frac": round(ach / fp_peak_tf, 4),
                 "peak_source": ("derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"
                                 if args.dtype == "f32" else "nominal GB300 FP64 rate 1.25 TFLOP/s")}
-    traffic = recorded_traffic(kernel_key)
+    traffic = recorded_traffic(kernel_key, args.workload)
     roof["traffic"] = traffic
     roof["kernel"] = f"{'tall' if args.workload == 'tall' else 'rankk'} {args.dtype} m={m} n={n} k={k} beta={beta}"
     roof["alg_bytes_per_launch"] = alg_bytes(m, n, k, beta, es)

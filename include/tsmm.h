@@ -72,6 +72,20 @@ typedef enum {
     TSMM_ERR_TIMEOUT = 7           /* a bounded device-side wait gave up (see tsmm_plan_check) */
 } tsmm_status;
 
+/*
+ * Arithmetic of a plan / packed B.  NATIVE: IEEE fma in the working precision
+ * (the contract stated above).  BF16X3 (TSMM_F32, regime (i) only): the
+ * tensor-core mode C = alpha*(A_hi*B_hi + A_hi*B_lo + A_lo*B_hi) + beta*C0
+ * with x_hi = bf16(x), x_lo = bf16(x - x_hi) and FP32 accumulation in tensor
+ * memory (tcgen05.mma).  It drops A_lo*B_lo and the split residues, about
+ * 3*2^-16 of |A||B| per product, so it does NOT meet the native bound for
+ * small k; its documented bound is |C - C_exact| <= (2^-13 + 4*k*2^-24) *
+ * (|alpha| sum_p |A[i,p]||B[p,j]| + |beta||C0[i,j]|).  Inf/NaN inputs may turn
+ * into NaN (the split of an infinity is Inf - Inf).  It needs a 16-byte
+ * aligned A with lda*4 a multiple of 16 (else TSMM_ERR_MISALIGNED).
+ */
+typedef enum { TSMM_PREC_NATIVE = 0, TSMM_PREC_BF16X3 = 1 } tsmm_precision;
+
 typedef void *tsmm_stream_t; /* a cudaStream_t */
 typedef struct tsmm_packed_b_s *tsmm_packed_b;
 typedef struct tsmm_plan_s *tsmm_plan_t;
@@ -105,6 +119,19 @@ TSMM_API int tsmm_version(void);
  */
 TSMM_API tsmm_status tsmm_pack_b(tsmm_dtype dtype, int64_t k, int64_t n, const void *B_dev, int64_t ldb,
                         tsmm_stream_t stream, tsmm_packed_b *out);
+
+/*
+ * tsmm_pack_b_ex -- tsmm_pack_b with an explicit precision mode.  BF16X3 packs
+ * B once as hi and lo BF16 copies in the tensor-core operand layout: per
+ * 64-row chunk c of k (kp = k rounded up to 64), a hi tile then a lo tile, each
+ * w x 64 BF16 values (w = n rounded up to a power of two, at least 16), element
+ * (column j, row kk) at byte (j/8)*1024 + (kk/8)*128 + (j%8)*16 + (kk%8)*2 of
+ * the tile.  INVALID_ARG for BF16X3 with TSMM_F64; UNSUPPORTED_SHAPE for
+ * BF16X3 with n > 64.
+ */
+TSMM_API tsmm_status tsmm_pack_b_ex(tsmm_dtype dtype, tsmm_precision precision, int64_t k, int64_t n,
+                                    const void *B_dev, int64_t ldb, tsmm_stream_t stream,
+                                    tsmm_packed_b *out);
 
 /* Release a packed B (waits for the device to be done with it).  NULL is a no-op. */
 TSMM_API tsmm_status tsmm_packed_b_destroy(tsmm_packed_b pb);
@@ -140,6 +167,13 @@ TSMM_API tsmm_status tsmm_packed_b_read(tsmm_packed_b pb, void *host_dst, size_t
  * UNSUPPORTED_SHAPE, OUT_OF_MEMORY, CUDA.
  */
 TSMM_API tsmm_status tsmm_plan(int64_t m, int64_t n, int64_t k, tsmm_dtype dtype, tsmm_plan_t *out);
+
+/*
+ * tsmm_plan_ex -- tsmm_plan with an explicit precision mode; the plan and the
+ * packed B given to tsmm_execute must have the same mode (else MISMATCH).
+ */
+TSMM_API tsmm_status tsmm_plan_ex(int64_t m, int64_t n, int64_t k, tsmm_dtype dtype,
+                                  tsmm_precision precision, tsmm_plan_t *out);
 
 /* Release a plan (waits for the device to be done with it).  NULL is a no-op. */
 TSMM_API tsmm_status tsmm_plan_destroy(tsmm_plan_t plan);

@@ -25,7 +25,8 @@ import os
 from . import build as _build
 
 __all__ = [
-    "TsmmError", "F32", "F64", "lib", "library_path",
+    "TsmmError", "F32", "F64", "PREC_NATIVE", "PREC_BF16X3", "lib", "library_path",
+    "tsmm_pack_b_ex", "tsmm_plan_ex",
     "tsmm_status_string", "tsmm_version", "tsmm_pack_b", "tsmm_packed_b_destroy",
     "tsmm_packed_b_info", "tsmm_packed_b_read", "tsmm_plan", "tsmm_plan_destroy", "tsmm_plan_info", "tsmm_execute",
     "tsmm_plan_check", "tsmm_plan_launches_per_execute", "tsmm_autotune",
@@ -35,6 +36,7 @@ __all__ = [
 ]
 
 F32, F64 = 0, 1
+PREC_NATIVE, PREC_BF16X3 = 0, 1
 STATUS = {
     0: "TSMM_OK", 1: "TSMM_ERR_INVALID_ARG", 2: "TSMM_ERR_UNSUPPORTED_SHAPE",
     3: "TSMM_ERR_MISMATCH", 4: "TSMM_ERR_MISALIGNED", 5: "TSMM_ERR_OUT_OF_MEMORY",
@@ -71,6 +73,10 @@ def _load():
     L.tsmm_version.argtypes = []
     L.tsmm_pack_b.restype = ci
     L.tsmm_pack_b.argtypes = [ci, i64, i64, vp, i64, vp, ctypes.POINTER(vp)]
+    L.tsmm_pack_b_ex.restype = ci
+    L.tsmm_pack_b_ex.argtypes = [ci, ci, i64, i64, vp, i64, vp, ctypes.POINTER(vp)]
+    L.tsmm_plan_ex.restype = ci
+    L.tsmm_plan_ex.argtypes = [i64, i64, i64, ci, ci, ctypes.POINTER(vp)]
     L.tsmm_packed_b_destroy.restype = ci
     L.tsmm_packed_b_destroy.argtypes = [vp]
     L.tsmm_packed_b_info.restype = ci
@@ -125,6 +131,20 @@ def tsmm_pack_b(dtype: int, k: int, n: int, B_dev: int, ldb: int, stream: int = 
     out = ctypes.c_void_p()
     _check(lib.tsmm_pack_b(dtype, k, n, B_dev or None, ldb, stream or None, ctypes.byref(out)),
            "tsmm_pack_b")
+    return out.value
+
+
+def tsmm_pack_b_ex(dtype: int, precision: int, k: int, n: int, B_dev: int, ldb: int,
+                   stream: int = 0) -> int:
+    out = ctypes.c_void_p()
+    _check(lib.tsmm_pack_b_ex(dtype, precision, k, n, B_dev or None, ldb, stream or None,
+                              ctypes.byref(out)), "tsmm_pack_b_ex")
+    return out.value
+
+
+def tsmm_plan_ex(m: int, n: int, k: int, dtype: int, precision: int) -> int:
+    out = ctypes.c_void_p()
+    _check(lib.tsmm_plan_ex(m, n, k, dtype, precision, ctypes.byref(out)), "tsmm_plan_ex")
     return out.value
 
 
@@ -250,7 +270,11 @@ def ld_of(t) -> int:
         raise ValueError("expected a 2-D tensor")
     if t.shape[0] > 1 and t.stride(0) != 1:
         raise ValueError("tensor is not column-major (stride(0) != 1)")
-    return int(t.stride(1)) if t.shape[1] > 1 else max(1, int(t.shape[0]))
+    rows = max(1, int(t.shape[0]))
+    if t.shape[1] > 1:
+        return int(t.stride(1))
+    # one column: its stride is free; keep it when it is a valid leading dimension
+    return int(t.stride(1)) if t.stride(1) >= rows else rows
 
 
 class PackedB:
@@ -310,18 +334,22 @@ class Plan:
             pass
 
 
-def pack_b(B, stream=None) -> PackedB:
+def pack_b(B, stream=None, precision: int = PREC_NATIVE) -> PackedB:
     """Pack a column-major k x n CUDA tensor (enqueued on the current stream)."""
     k, n = B.shape
     dt = _dtype_code(B.dtype)
-    h = tsmm_pack_b(dt, k, n, B.data_ptr() if B.numel() else 0, ld_of(B) if k else 1,
-                    _stream_handle(stream))
-    return PackedB(h, k, n, dt)
+    h = tsmm_pack_b_ex(dt, precision, k, n, B.data_ptr() if B.numel() else 0,
+                       ld_of(B) if k else 1, _stream_handle(stream))
+    pb = PackedB(h, k, n, dt)
+    pb.precision = precision
+    return pb
 
 
-def plan(m: int, n: int, k: int, dtype) -> Plan:
+def plan(m: int, n: int, k: int, dtype, precision: int = PREC_NATIVE) -> Plan:
     dt = dtype if isinstance(dtype, int) else _dtype_code(dtype)
-    return Plan(tsmm_plan(m, n, k, dt), m, n, k, dt)
+    p = Plan(tsmm_plan_ex(m, n, k, dt, precision), m, n, k, dt)
+    p.precision = precision
+    return p
 
 
 def execute_grouped(problems, stream=None) -> None:

@@ -99,24 +99,37 @@ int tsmm_version(void) { return kVersion; }
 
 tsmm_status tsmm_pack_b(tsmm_dtype dtype, int64_t k, int64_t n, const void *B_dev, int64_t ldb,
                         tsmm_stream_t stream, tsmm_packed_b *out) {
+    return tsmm_pack_b_ex(dtype, TSMM_PREC_NATIVE, k, n, B_dev, ldb, stream, out);
+}
+
+tsmm_status tsmm_pack_b_ex(tsmm_dtype dtype, tsmm_precision precision, int64_t k, int64_t n,
+                           const void *B_dev, int64_t ldb, tsmm_stream_t stream, tsmm_packed_b *out) {
     if (!out || !valid_dtype(dtype) || k < 0 || n < 0) return TSMM_ERR_INVALID_ARG;
+    if (precision != TSMM_PREC_NATIVE && precision != TSMM_PREC_BF16X3) return TSMM_ERR_INVALID_ARG;
+    if (precision == TSMM_PREC_BF16X3 && dtype != TSMM_F32) return TSMM_ERR_INVALID_ARG;
     if (ldb < std::max<int64_t>(1, k)) return TSMM_ERR_INVALID_ARG;
     if (k > 0 && n > 0 && !B_dev) return TSMM_ERR_INVALID_ARG;
     const size_t es = dtype_size(dtype);
     if (B_dev && !aligned(B_dev, es)) return TSMM_ERR_MISALIGNED;
     const int regime = regime_of(k, n);
-    if (regime == 0) return TSMM_ERR_UNSUPPORTED_SHAPE;
+    if (regime == 0 || (precision == TSMM_PREC_BF16X3 && regime != 1))
+        return TSMM_ERR_UNSUPPORTED_SHAPE;
     const int dev = current_device();
     if (dev < 0) return TSMM_ERR_CUDA;
 
     tsmm_packed_b pb = new (std::nothrow) tsmm_packed_b_s();
     if (!pb) return TSMM_ERR_OUT_OF_MEMORY;
     pb->dtype = dtype;
+    pb->precision = precision;
     pb->k = k;
     pb->n = n;
     pb->regime = regime;
     pb->device = dev;
-    if (regime == 1) {
+    if (precision == TSMM_PREC_BF16X3) {
+        pb->kp = round_up(k, kX3KB);
+        pb->w = x3_np(n);
+        pb->ntiles = 1;
+    } else if (regime == 1) {
         pb->kp = round_up(k, kTallBKS);
         pb->w = tall_np(n);
         pb->ntiles = 1;
@@ -125,7 +138,9 @@ tsmm_status tsmm_pack_b(tsmm_dtype dtype, int64_t k, int64_t n, const void *B_de
         pb->w = kRankNT;
         pb->ntiles = (n + kRankNT - 1) / kRankNT;
     }
-    pb->bytes = (size_t)(pb->kp * pb->w * pb->ntiles) * es;
+    // BF16x3: a hi and a lo BF16 copy of every element
+    pb->bytes = precision == TSMM_PREC_BF16X3 ? (size_t)(pb->kp * pb->w) * 2 * 2
+                                              : (size_t)(pb->kp * pb->w * pb->ntiles) * es;
     pb->data = nullptr;
     if (pb->bytes > 0) {
         cudaError_t e = cudaMalloc(&pb->data, pb->bytes);
@@ -134,8 +149,11 @@ tsmm_status tsmm_pack_b(tsmm_dtype dtype, int64_t k, int64_t n, const void *B_de
             delete pb;
             return cuda_status(e);
         }
-        e = launch_pack_b(dtype, k, n, B_dev, ldb, pb->data, pb->kp, pb->w, pb->ntiles,
-                          static_cast<cudaStream_t>(stream));
+        e = precision == TSMM_PREC_BF16X3
+                ? launch_pack_b_bf16x3(k, n, B_dev, ldb, pb->data, (int)pb->w, pb->kp / kX3KB,
+                                       static_cast<cudaStream_t>(stream))
+                : launch_pack_b(dtype, k, n, B_dev, ldb, pb->data, pb->kp, pb->w, pb->ntiles,
+                                static_cast<cudaStream_t>(stream));
         if (e != cudaSuccess) {
             cudaFree(pb->data);
             delete pb;
@@ -177,14 +195,21 @@ tsmm_status tsmm_packed_b_read(tsmm_packed_b pb, void *host_dst, size_t bytes) {
 }
 
 tsmm_status tsmm_plan(int64_t m, int64_t n, int64_t k, tsmm_dtype dtype, tsmm_plan_t *out) {
+    return tsmm_plan_ex(m, n, k, dtype, TSMM_PREC_NATIVE, out);
+}
+
+tsmm_status tsmm_plan_ex(int64_t m, int64_t n, int64_t k, tsmm_dtype dtype, tsmm_precision precision,
+                         tsmm_plan_t *out) {
     if (!out || !valid_dtype(dtype) || m < 0 || n < 0 || k < 0) return TSMM_ERR_INVALID_ARG;
+    if (precision != TSMM_PREC_NATIVE && precision != TSMM_PREC_BF16X3) return TSMM_ERR_INVALID_ARG;
+    if (precision == TSMM_PREC_BF16X3 && dtype != TSMM_F32) return TSMM_ERR_INVALID_ARG;
     int dev = current_device();
     int sms = 0;
     if (dev >= 0 && cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         sms = 0;
-    // a tuned choice recorded in the plan cache wins over the heuristic
-    const int cached = plan_cache_lookup(dtype, m, n, k, sms);
-    return create_plan(m, n, k, dtype, cached, out);
+    // a tuned choice recorded in the plan cache wins over the heuristic (native precision)
+    const int cached = precision == TSMM_PREC_NATIVE ? plan_cache_lookup(dtype, m, n, k, sms) : 0;
+    return create_plan(m, n, k, dtype, cached, out, precision);
 }
 
 }  // extern "C"
@@ -192,10 +217,11 @@ tsmm_status tsmm_plan(int64_t m, int64_t n, int64_t k, tsmm_dtype dtype, tsmm_pl
 namespace tsmm {
 
 tsmm_status create_plan(int64_t m, int64_t n, int64_t k, tsmm_dtype dtype, int forced_splits,
-                        tsmm_plan_t *out) {
+                        tsmm_plan_t *out, int precision) {
     if (!out || !valid_dtype(dtype) || m < 0 || n < 0 || k < 0) return TSMM_ERR_INVALID_ARG;
     const int regime = regime_of(k, n);
-    if (regime == 0) return TSMM_ERR_UNSUPPORTED_SHAPE;
+    if (regime == 0 || (precision == TSMM_PREC_BF16X3 && regime != 1))
+        return TSMM_ERR_UNSUPPORTED_SHAPE;
     const int dev = current_device();
     if (dev < 0) return TSMM_ERR_CUDA;
     int sms = 0;
@@ -209,12 +235,35 @@ tsmm_status create_plan(int64_t m, int64_t n, int64_t k, tsmm_dtype dtype, int f
     p->n = n;
     p->k = k;
     p->dtype = dtype;
+    p->precision = precision;
     p->regime = regime;
     p->device = dev;
     p->num_sms = sms;
     const size_t es = dtype_size(dtype);
     size_t ticket_bytes = 0;
-    if (regime == 1) {
+    if (precision == TSMM_PREC_BF16X3) {
+        // one 128-row slab per block, k in 64-column chunks, one block per SM
+        p->np = x3_np(n);
+        p->bm = 128;
+        p->kp = round_up(k, kX3KB);
+        p->slabs = (m + p->bm - 1) / p->bm;
+        const int64_t kstages = p->kp / kX3KB;
+        const int64_t per_split = (int64_t)p->np * p->slabs * p->bm * (int64_t)es;
+        int64_t max_splits = 65535;
+        if (per_split > 0) max_splits = std::min<int64_t>(max_splits, (512LL << 20) / per_split);
+        int s = (kstages > 0 && p->slabs > 0)
+                    ? choose_splits(p->slabs, kstages, sms, max_splits, 1)
+                    : 1;
+        if (forced_splits > 0)
+            s = (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)forced_splits, kstages, max_splits}));
+        const int64_t chunk_stages = kstages > 0 ? (kstages + s - 1) / s : 1;
+        p->kchunk = chunk_stages * kX3KB;
+        p->splits = kstages > 0 ? (int)((kstages + chunk_stages - 1) / chunk_stages) : 1;
+        if (p->splits > 1) {
+            p->workspace_bytes = (size_t)p->splits * (size_t)per_split;
+            ticket_bytes = (size_t)p->slabs * sizeof(unsigned);
+        }
+    } else if (regime == 1) {
         p->np = tall_np(n);
         p->bm = tall_bm(dtype);
         p->kp = round_up(k, kTallBKS);
@@ -301,7 +350,8 @@ tsmm_status tsmm_execute(tsmm_plan_t p, double alpha, const void *A_dev, int64_t
                          tsmm_packed_b pb, double beta, void *C_dev, int64_t ldc,
                          tsmm_stream_t stream) {
     if (!p || !pb) return TSMM_ERR_INVALID_ARG;
-    if (pb->dtype != p->dtype || pb->k != p->k || pb->n != p->n || pb->device != p->device)
+    if (pb->dtype != p->dtype || pb->k != p->k || pb->n != p->n || pb->device != p->device ||
+        pb->precision != p->precision)
         return TSMM_ERR_MISMATCH;
     if (current_device() != p->device) return TSMM_ERR_MISMATCH;
     const int64_t m = p->m, n = p->n, k = p->k;
@@ -358,6 +408,10 @@ tsmm_status tsmm_execute(tsmm_plan_t p, double alpha, const void *A_dev, int64_t
         }
         p->tmap_ptr = A_dev;
         p->tmap_lda = lda;
+    }
+    if (p->precision == TSMM_PREC_BF16X3) {
+        if (!tma) return TSMM_ERR_MISALIGNED;  // this mode streams A with TMA only
+        return cuda_status(launch_tall_bf16x3(p->np, &p->tmap, a, s));
     }
     if (p->regime == 2) {
         RankArgs ra;

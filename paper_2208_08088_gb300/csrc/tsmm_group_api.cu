@@ -45,7 +45,8 @@ tsmm_status validate(const tsmm_group_item &it) {
     tsmm_plan_t p = it.plan;
     tsmm_packed_b pb = it.pb;
     if (!p || !pb) return TSMM_ERR_INVALID_ARG;
-    if (pb->dtype != p->dtype || pb->k != p->k || pb->n != p->n || pb->device != p->device)
+    if (pb->dtype != p->dtype || pb->k != p->k || pb->n != p->n || pb->device != p->device ||
+        pb->precision != p->precision)
         return TSMM_ERR_MISMATCH;
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess) return TSMM_ERR_CUDA;
@@ -65,7 +66,7 @@ bool groupable(const tsmm_group_item &it) {
     const size_t es = dtype_size(p->dtype);
     const bool alpha_zero = it.alpha == 0.0 ||
                             (p->dtype == TSMM_F32 && static_cast<float>(it.alpha) == 0.0f);
-    return p->regime == 1 && p->m > 0 && p->n > 0 && p->k > 0 && !alpha_zero &&
+    return p->regime == 1 && p->precision == TSMM_PREC_NATIVE && p->m > 0 && p->n > 0 && p->k > 0 && !alpha_zero &&
            is_aligned(it.A_dev, 16) && (it.lda * (int64_t)es) % 16 == 0 && p->m < INT_MAX &&
            p->k < INT_MAX && (it.lda * (int64_t)es) < (1LL << 40) && encoder_grouped() != nullptr;
 }

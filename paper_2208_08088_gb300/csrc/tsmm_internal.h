@@ -50,6 +50,7 @@ inline int64_t round_up(int64_t x, int64_t g) { return (x + g - 1) / g * g; }
 
 struct tsmm_packed_b_s {
     tsmm_dtype dtype;
+    int precision;   // tsmm_precision
     int64_t k, n;
     int64_t kp;      // padded rows
     int64_t w;       // tile width (columns)
@@ -63,6 +64,7 @@ struct tsmm_packed_b_s {
 struct tsmm_plan_s {
     int64_t m, n, k;
     tsmm_dtype dtype;
+    int precision;   // tsmm_precision
     int regime;
     int device;
     int num_sms;
@@ -126,7 +128,17 @@ cudaError_t launch_rankk(tsmm_dtype dt, const CUtensorMap *tmA, const CUtensorMa
 
 // Plan construction with an optional forced split count (0 = planner's choice).
 tsmm_status create_plan(int64_t m, int64_t n, int64_t k, tsmm_dtype dtype, int forced_splits,
-                        tsmm_plan_t *out);
+                        tsmm_plan_t *out, int precision = 0);
+
+// BF16x3 precision mode (tsmm_bf16x3.cu): k granule of its packed B and plan.
+constexpr int kX3KB = 64;
+inline int x3_np(int64_t n) {
+    const int np = tall_np(n);
+    return np < 16 ? 16 : np;
+}
+cudaError_t launch_tall_bf16x3(int np, const CUtensorMap *tmap, const TallArgs &a, cudaStream_t s);
+cudaError_t launch_pack_b_bf16x3(int64_t k, int64_t n, const void *B, int64_t ldb, void *dst, int np,
+                                 int64_t nchunks, cudaStream_t s);
 
 // Process-wide plan cache (tsmm_tune.cu): tuned split counts keyed by
 // (dtype, m, n, k, SM count).  Lookup returns 0 when absent.

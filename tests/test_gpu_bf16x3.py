@@ -1,0 +1,151 @@
+"""BF16x3 precision mode (tcgen05 tensor cores, FP32 accumulation in TMEM).
+
+Integer-valued inputs in [-4, 4] are exact in BF16 (x_lo = 0) and every
+partial sum is exact in FP32, so the tensor-core result must equal the oracle
+bit for bit -- this pins the operand layouts, the k chunking and the split-K
+finish exactly.  General inputs are checked against the mode's stated bound
+(2^-13 + 4*k*2^-24) * (|alpha||A||B| + |beta||C0|)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2208_08088_gb300 as tsmm
+import tsmm_inputs as ti
+from gpu_util import to_device
+
+pytestmark = pytest.mark.gpu
+X3 = tsmm.PREC_BF16X3
+
+
+def run_x3(A, B, C0, alpha, beta, lda=None, a_offset=0, repeats=1):
+    m, k = A.shape
+    n = B.shape[1]
+    if lda is None:
+        lda = (m + 3) // 4 * 4  # this mode needs lda*4 to be a multiple of 16
+    dA = to_device(A, lda, a_offset)
+    pb = tsmm.pack_b(to_device(B), precision=X3)
+    pl = tsmm.plan(m, n, k, torch.float32, precision=X3)
+    outs = []
+    for _ in range(repeats):
+        dC = to_device(C0 if C0 is not None else np.full((m, n), np.nan, np.float32, order="F"))
+        tsmm.execute(pl, alpha, dA, pb, beta, dC)
+        pl.check()
+        outs.append(dC.cpu().numpy())
+    return outs if repeats > 1 else outs[0], pl
+
+
+def x3_bound(A, B, C0, alpha, beta):
+    k = A.shape[1]
+    G = np.abs(A.astype(np.float64)) @ np.abs(B.astype(np.float64))
+    c = np.abs(C0.astype(np.float64)) if C0 is not None else 0.0
+    return (2.0 ** -13 + 4 * k * 2.0 ** -24) * (abs(alpha) * G + abs(beta) * c)
+
+
+@pytest.mark.parametrize("m,n,k", [(1000, 64, 777), (300, 16, 20000), (129, 17, 64), (2048, 32, 2048),
+                                   (5, 3, 1), (640, 64, 4096), (257, 40, 130)])
+def test_bf16x3_integer_bit_exact(m, n, k):
+    A = ti.matrix_np(m, k, 21, "integer", np.float32)
+    B = ti.matrix_np(k, n, 22, "integer", np.float32)
+    C0 = ti.matrix_np(m, n, 23, "integer", np.float32)
+    C, pl = run_x3(A, B, C0, 1.5, 0.5)
+    Cref, _ = oracle.tsmm(1.5, A, B, 0.5, C0)
+    np.testing.assert_array_equal(C, oracle.round_to(Cref, np.float32))
+
+
+@pytest.mark.parametrize("m,n,k,beta", [(1000, 64, 777, 1.0), (300, 16, 20000, 0.0), (2048, 32, 2048, -0.5),
+                                        (4096, 64, 6000, 1.0), (77, 9, 100, 1.0)])
+def test_bf16x3_uniform_within_mode_bound(m, n, k, beta):
+    A = ti.matrix_np(m, k, 31, "uniform", np.float32)
+    B = ti.matrix_np(k, n, 32, "uniform", np.float32)
+    C0 = ti.matrix_np(m, n, 33, "uniform", np.float32)
+    C, pl = run_x3(A, B, C0 if beta != 0 else None, 1.25, beta)
+    Cref, _ = oracle.tsmm(1.25, A, B, beta, C0 if beta != 0 else None)
+    E3 = x3_bound(A, B, C0 if beta != 0 else None, 1.25, beta)
+    err = np.abs(C.astype(np.float64) - Cref)
+    assert np.all(np.isfinite(C))
+    assert np.all(err <= E3), f"max err/bound {np.max(err / E3):.3g}"
+
+
+def test_bf16x3_deterministic_split_k():
+    A = ti.matrix_np(700, 30000, 41, "uniform", np.float32)
+    B = ti.matrix_np(30000, 64, 42, "uniform", np.float32)
+    C0 = ti.matrix_np(700, 64, 43, "uniform", np.float32)
+    outs, pl = run_x3(A, B, C0, 1.0, 1.0, repeats=3)
+    assert pl.info()["splits"] > 1
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[1], outs[2])
+
+
+def test_bf16x3_errors():
+    B = to_device(ti.matrix_np(100, 16, 1, "uniform", np.float32))
+    pb_native = tsmm.pack_b(B)
+    pl_x3 = tsmm.plan(50, 16, 100, torch.float32, precision=X3)
+    A = to_device(ti.matrix_np(50, 100, 1, "uniform", np.float32))
+    C = to_device(np.zeros((50, 16), np.float32, order="F"))
+    with pytest.raises(tsmm.TsmmError) as e:  # mode mismatch between plan and packed B
+        tsmm.execute(pl_x3, 1.0, A, pb_native, 0.0, C)
+    assert e.value.status == 3
+    with pytest.raises(tsmm.TsmmError) as e:  # FP64 has no BF16x3 mode
+        tsmm.plan(50, 16, 100, torch.float64, precision=X3)
+    assert e.value.status == 1
+    with pytest.raises(tsmm.TsmmError) as e:  # regime (ii) not in this mode
+        tsmm.plan(500, 200, 64, torch.float32, precision=X3)
+    assert e.value.status == 2
+    pb = tsmm.pack_b(B, precision=X3)
+    A_odd = to_device(ti.matrix_np(50, 100, 1, "uniform", np.float32), offset=1)
+    with pytest.raises(tsmm.TsmmError) as e:  # TMA-only mode: unaligned A
+        tsmm.execute(pl_x3, 1.0, A_odd, pb, 0.0, C)
+    assert e.value.status == 4
+
+
+def test_bf16x3_pack_layout_roundtrip():
+    """hi + lo of every packed element reproduces B to BF16x2 accuracy, and the
+    hi/lo tiles sit where the layout documented in tsmm.h puts them."""
+    k, n = 130, 40
+    B = ti.matrix_np(k, n, 51, "uniform", np.float32)
+    pb = tsmm.pack_b(to_device(B), precision=X3)
+    info = pb.info()
+    kp, w = info["kp"], info["w"]
+    assert kp == 192 and w == 64 and info["bytes"] == kp * w * 4
+    raw = np.empty(info["bytes"] // 2, dtype=np.uint16)
+    tsmm.tsmm_packed_b_read(pb.handle, raw.ctypes.data, raw.nbytes)
+
+    def bf16(u):
+        return (u.astype(np.uint32) << 16).view(np.float32)
+
+    rec = np.zeros((kp, w), dtype=np.float64)
+    for c in range(kp // 64):
+        base = c * 2 * w * 64
+        for j in range(w):
+            for kk in range(64):
+                off = ((j // 8) * 1024 + (kk // 8) * 128 + (j % 8) * 16 + (kk % 8) * 2) // 2
+                rec[c * 64 + kk, j] = float(bf16(raw[base + off : base + off + 1])[0]) + \
+                    float(bf16(raw[base + w * 64 + off : base + w * 64 + off + 1])[0])
+    err = np.abs(rec[:k, :n] - B.astype(np.float64))
+    assert np.all(err <= 2.0 ** -16 * np.abs(B))
+    assert np.all(rec[k:, :] == 0) and np.all(rec[:, n:] == 0)
+
+
+def test_bf16x3_full_size_sampled():
+    """m = k = 32768, n = 64 (the FP32 sweep's FMA-bound point) in this mode."""
+    m = k = 32768
+    n = 64
+    dA = torch.empty((k, m), dtype=torch.float32, device="cuda")
+    ti.fill_torch(dA, ti.SEED_A, "uniform")
+    dA = dA.t()
+    dB = torch.empty((n, k), dtype=torch.float32, device="cuda")
+    ti.fill_torch(dB, ti.SEED_B, "uniform")
+    dB = dB.t()
+    pl = tsmm.plan(m, n, k, torch.float32, precision=X3)
+    pb = tsmm.pack_b(dB, precision=X3)
+    dC = torch.zeros((n, m), dtype=torch.float32, device="cuda").t()
+    tsmm.execute(pl, 1.0, dA, pb, 0.0, dC)
+    pl.check()
+    rows = np.sort(np.random.default_rng(3).choice(m, 32, replace=False))
+    A_r = np.asfortranarray(ti.rows_np(rows, m, k, ti.SEED_A, "uniform", np.float32))
+    B = ti.matrix_np(k, n, ti.SEED_B, "uniform", np.float32)
+    Cref, _ = oracle.tsmm(1.0, A_r, B, 0.0, None)
+    C = dC[torch.as_tensor(rows, device="cuda")].cpu().numpy()
+    E3 = x3_bound(A_r, B, None, 1.0, 0.0)
+    err = np.abs(C.astype(np.float64) - Cref)
+    assert np.all(err <= E3), f"max err/bound {np.max(err / E3):.3g}"

@@ -54,7 +54,9 @@ def parse():
     p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--dtype", choices=["f32", "f64"], default="f32")
-    p.add_argument("--workload", choices=["tall", "rankk"], default="tall")
+    p.add_argument("--workload", choices=["tall", "rankk", "precision"], default="tall")
+    p.add_argument("--precision", choices=["native", "bf16x3"], default="native",
+                   help="arithmetic of the tall sweep: IEEE FMA (default) or the BF16x3 tensor-core mode")
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--size", type=int, default=None,
                    help="profiling/small runs: m = k (tall) or m = n (rankk) instead of the workload's")
@@ -92,8 +94,9 @@ def workload_name(args):
         return "reduced case for profiling: " + ", ".join(
             f"m={m} n={n} k={k} beta={b}" for (m, n, k, b) in workload_points(args))
     if args.workload == "tall":
+        mode = "" if args.precision == "native" else " in the BF16x3 tensor-core mode"
         return (f"memory-bound sweep {args.dtype.upper()} m=k=32768, n in {SWEEP_N}, "
-                f"beta in {{0,1}}, alpha=1, B pre-packed and reused")
+                f"beta in {{0,1}}, alpha=1, B pre-packed and reused{mode}")
     return f"rank-k {args.dtype.upper()} m=n=16384, k in {RANKK_K}, beta=1, B pre-packed"
 
 
@@ -327,10 +330,11 @@ def run_ours(args):
         if (m, k) not in A:
             A[(m, k)] = dmat(m, k, ti.SEED_A)
     packed, plans, C = {}, {}, {}
+    prec = tsmm.PREC_BF16X3 if args.precision == "bf16x3" else tsmm.PREC_NATIVE
     for (m, n, k, beta) in pts:
         if (n, k) not in packed:
-            packed[(n, k)] = tsmm.pack_b(dmat(k, n, ti.SEED_B))
-            plans[(m, n, k)] = tsmm.plan(m, n, k, tdt)
+            packed[(n, k)] = tsmm.pack_b(dmat(k, n, ti.SEED_B), precision=prec)
+            plans[(m, n, k)] = tsmm.plan(m, n, k, tdt, precision=prec)
             C[(m, n)] = dmat(m, n, ti.SEED_C0)  # C0; beta = 1 updates it in place
     torch.cuda.synchronize()
 
@@ -384,6 +388,14 @@ def run_ours(args):
     hbm_peak, hbm_src = load_peaks()
     fp32_peak_tf = SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
     fp_peak_tf = fp32_peak_tf if args.dtype == "f32" else FP64_NOMINAL_TFLOPS
+    if args.precision == "bf16x3":
+        # three BF16 tensor-core products per FP32 product: the measured dense
+        # BF16 peak / 3 (MEASURED_PEAKS.json bf16_tflops)
+        try:
+            with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+                fp_peak_tf = float(json.load(f)["bf16_tflops"]) / 3.0
+        except Exception:
+            fp_peak_tf = 1900.0 / 3.0
 
     points = []
     for pt in pts:
@@ -506,10 +518,80 @@ def run_e2e(args, tsmm, torch, tdt, es, pts, A, packed, plans, world):
             "ms_per_step": round(ms / steps, 3)}
 
 
+def run_precision(args):
+    """Precision-mode workload: m = k = 32768, n = 64, A and B entries
+    N(0,1) * 10**U[-3,3] per row, computed in FP32 (IEEE FMA), in the BF16x3
+    tensor-core mode, and in FP64 (FMA) on the same inputs; each result's
+    error against the FP64 oracle on sampled rows, and each launch's time."""
+    import torch
+
+    import oracle
+    import paper_2208_08088_gb300 as tsmm
+    import tsmm_inputs as ti
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    m = k = args.size or 32768
+    n = args.only or 64
+    A32 = torch.empty((k, m), dtype=torch.float32, device="cuda")
+    ti.normal_scaled_torch(A32, ti.SEED_A)
+    A32 = A32.t()
+    B32 = torch.empty((n, k), dtype=torch.float32, device="cuda")
+    ti.normal_scaled_torch(B32, ti.SEED_B)
+    B32 = B32.t()
+    rows = np.sort(np.random.default_rng(7).choice(m, 64, replace=False))
+    A_rows = np.asfortranarray(A32[torch.as_tensor(rows, device="cuda")].cpu().numpy().astype(np.float64))
+    B_host = np.asfortranarray(B32.cpu().numpy().astype(np.float64))
+    Cref, _ = oracle.tsmm(1.0, A_rows, B_host, 0.0, None)
+    G = np.abs(A_rows) @ np.abs(B_host)
+    results = []
+    for name, dt, prec in (("fp32_fma", torch.float32, tsmm.PREC_NATIVE),
+                           ("bf16x3_tcgen05", torch.float32, tsmm.PREC_BF16X3),
+                           ("fp64_fma", torch.float64, tsmm.PREC_NATIVE)):
+        A = A32 if dt == torch.float32 else A32.t().double().t()
+        B = B32 if dt == torch.float32 else B32.t().double().t()
+        pb = tsmm.pack_b(B, precision=prec)
+        pl = tsmm.plan(m, n, k, dt, precision=prec)
+        C = torch.zeros((n, m), dtype=dt, device="cuda").t()
+        for _ in range(args.warmup):
+            tsmm.execute(pl, 1.0, A, pb, 0.0, C)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            tsmm.execute(pl, 1.0, A, pb, 0.0, C)
+        e1.record()
+        torch.cuda.synchronize()
+        pl.check()
+        ms = e0.elapsed_time(e1) / args.steps
+        Cs = C[torch.as_tensor(rows, device="cuda")].cpu().numpy().astype(np.float64)
+        err = np.abs(Cs - Cref)
+        results.append({"mode": name, "avg_ms": round(ms, 4),
+                        "gflops": round(flops(m, n, k) / (ms * 1e-3) / 1e9, 1),
+                        "max_abs_err_over_sum_abs": float(np.max(err / G)),
+                        "max_rel_err": float(np.max(err / np.maximum(np.abs(Cref), 1e-300))),
+                        "median_rel_err": float(np.median(err / np.maximum(np.abs(Cref), 1e-300)))})
+        del A, B, C, pb, pl
+        torch.cuda.empty_cache()
+    x3 = [r for r in results if r["mode"] == "bf16x3_tcgen05"][0]
+    line = {"metric": METRIC, "value": x3["gflops"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": x3["avg_ms"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 (bf16x3 tensor-core mode)",
+            "data": "synthetic",
+            "config": {"workload": f"precision mode m=k={m}, n={n}, A and B entries "
+                                   "N(0,1)*10^U[-3,3] per row, alpha=1, beta=0",
+                       "error_reference": "FP64 oracle (compensated Dot2) on 64 sampled rows"},
+            "modes": results}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "precision":
+        return run_precision(args)
     return run_ours(args)
 
 

@@ -80,3 +80,10 @@ def test_normal_scaled_shape_and_scale():
     assert Z.shape == (400, 300) and np.all(np.isfinite(Z))
     rs = np.abs(Z).max(axis=1)
     assert rs.max() / rs.min() > 1e3  # rows span several decades
+
+
+def test_normal_scaled_torch_matches_numpy():
+    t = torch.empty(6, 9, dtype=torch.float64)  # 9 x 6 column-major matrix
+    ti.normal_scaled_torch(t, 3, chunk=7)
+    Z = ti.normal_scaled_np(9, 6, 3, np.float64)
+    np.testing.assert_allclose(t.t().numpy(), Z, rtol=1e-13, atol=0)

@@ -158,3 +158,28 @@ def normal_scaled_np(rows: int, cols: int, seed: int, dtype=np.float32) -> np.nd
     e = (bits_np(ridx, seed, 13) >> 8).astype(np.float64) * 2.0 ** -24 * 6.0 - 3.0
     z = z.reshape(cols, rows).T * (10.0 ** e)[:, None]
     return np.asfortranarray(z.astype(dtype))
+
+
+def normal_scaled_torch(t, seed: int, chunk: int = 1 << 24):
+    """Device counterpart of normal_scaled_np: fill the contiguous storage of a
+    rows x cols column-major matrix viewed as t.t() (t has shape cols x rows)
+    with N(0,1) * 10**U[-3,3] (U drawn once per row) using torch float64 math
+    on t's device.  Transcendentals may differ from numpy's in the last bits,
+    so consumers that need the exact values read them back from the tensor."""
+    import torch
+
+    cols, rows = t.shape
+    flat = t.view(-1)
+    k1, k2, k3 = stream_key(seed, 11), stream_key(seed, 12), stream_key(seed, 13)
+    ridx = torch.arange(rows, dtype=torch.int64, device=t.device)
+    e = (_bits(ridx, k3) >> 8).to(torch.float64) * 2.0 ** -24 * 6.0 - 3.0
+    scale = torch.pow(torch.tensor(10.0, dtype=torch.float64, device=t.device), e)
+    n = flat.numel()
+    for start in range(0, n, chunk):
+        stop = min(n, start + chunk)
+        idx = torch.arange(start, stop, dtype=torch.int64, device=t.device)
+        u1 = ((_bits(idx, k1) >> 8).to(torch.float64) + 1.0) * 2.0 ** -24
+        u2 = (_bits(idx, k2) >> 8).to(torch.float64) * 2.0 ** -24
+        z = torch.sqrt(-2.0 * torch.log(u1)) * torch.cos(2.0 * math.pi * u2)
+        flat[start:stop] = (z * scale[idx % rows]).to(flat.dtype)
+    return t

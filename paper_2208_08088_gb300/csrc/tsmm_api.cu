@@ -411,7 +411,7 @@ tsmm_status tsmm_execute(tsmm_plan_t p, double alpha, const void *A_dev, int64_t
     }
     if (p->precision == TSMM_PREC_BF16X3) {
         if (!tma) return TSMM_ERR_MISALIGNED;  // this mode streams A with TMA only
-        return cuda_status(launch_tall_bf16x3(p->np, &p->tmap, a, s));
+        return cuda_status(launch_tall_bf16x3(p->np, &p->tmap, a, p->num_sms, s));
     }
     if (p->regime == 2) {
         RankArgs ra;

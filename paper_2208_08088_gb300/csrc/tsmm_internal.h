@@ -136,7 +136,8 @@ inline int x3_np(int64_t n) {
     const int np = tall_np(n);
     return np < 16 ? 16 : np;
 }
-cudaError_t launch_tall_bf16x3(int np, const CUtensorMap *tmap, const TallArgs &a, cudaStream_t s);
+cudaError_t launch_tall_bf16x3(int np, const CUtensorMap *tmap, const TallArgs &a, int num_sms,
+                               cudaStream_t s);
 cudaError_t launch_pack_b_bf16x3(int64_t k, int64_t n, const void *B, int64_t ldb, void *dst, int np,
                                  int64_t nchunks, cudaStream_t s);
 

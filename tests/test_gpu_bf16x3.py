@@ -43,7 +43,9 @@ def x3_bound(A, B, C0, alpha, beta):
 
 
 @pytest.mark.parametrize("m,n,k", [(1000, 64, 777), (300, 16, 20000), (129, 17, 64), (2048, 32, 2048),
-                                   (5, 3, 1), (640, 64, 4096), (257, 40, 130)])
+                                   (5, 3, 1), (640, 64, 4096), (257, 40, 130),
+                                   # several work items per persistent block, with and without split-K
+                                   (20000, 64, 4000), (40000, 32, 64)])
 def test_bf16x3_integer_bit_exact(m, n, k):
     A = ti.matrix_np(m, k, 21, "integer", np.float32)
     B = ti.matrix_np(k, n, 22, "integer", np.float32)

@@ -54,7 +54,9 @@ def parse():
     p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--dtype", choices=["f32", "f64"], default="f32")
-    p.add_argument("--workload", choices=["tall", "rankk", "precision"], default="tall")
+    p.add_argument("--workload", choices=["tall", "rankk", "precision", "serving"], default="tall")
+    p.add_argument("--requests", type=int, default=10000, help="serving: number of requests")
+    p.add_argument("--load", type=float, default=0.8, help="serving: arrival rate / measured capacity")
     p.add_argument("--precision", choices=["native", "bf16x3"], default="native",
                    help="arithmetic of the tall sweep: IEEE FMA (default) or the BF16x3 tensor-core mode")
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
@@ -586,8 +588,111 @@ def run_precision(args):
     return 0
 
 
+def run_serving(args):
+    """Serving workload: 32 device-resident packed B (k log-uniform in
+    [64, 8192], n log-uniform in [1, 64], drawn once from a seed); requests pick a
+    B uniformly and m log-uniform in [1024, 262144]; FP32, alpha = 1, beta = 0.
+    The server admits under a 40 GB budget and batches continuously (grouped
+    persistent launches on 4 streams).  Capacity is measured with every request
+    arriving at once; then Poisson arrivals at `--load` x capacity give the
+    p50 / p99 arrival-to-completion latency and the aggregate GFLOP/s."""
+    import torch
+
+    import paper_2208_08088_gb300 as tsmm
+    import tsmm_inputs as ti
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    rng = np.random.default_rng(2208)
+    NB = 32
+    ks = np.round(np.exp(rng.uniform(np.log(64), np.log(8192), NB))).astype(np.int64)
+    ns = np.round(np.exp(rng.uniform(np.log(1), np.log(64), NB))).astype(np.int64)
+    packed = []
+    for i in range(NB):
+        B = torch.empty((int(ns[i]), int(ks[i])), dtype=torch.float32, device="cuda")
+        ti.fill_torch(B, 100 + i, "uniform")
+        packed.append(tsmm.pack_b(B.t()))
+    N = args.requests
+    b_idx = rng.integers(NB, size=N)
+    ms = np.round(np.exp(rng.uniform(np.log(1024), np.log(262144), N))).astype(np.int64)
+    mk = ms * ks[b_idx]
+    mn = ms * ns[b_idx]
+    fl = 2.0 * ms * ns[b_idx] * ks[b_idx]
+    # A: windows into one resident pool (synthetic inputs already on the device);
+    # C: disjoint windows of a pool larger than the budget, reused in a ring
+    a_pool = torch.empty(int(mk.max()) + 1024, dtype=torch.float32, device="cuda")
+    ti.fill_torch(a_pool, ti.SEED_A, "uniform")
+    c_elems = (48 << 30) // 4
+    c_pool = torch.zeros(c_elems, dtype=torch.float32, device="cuda")
+    a_off = (rng.integers(0, (a_pool.numel() - mk) // 4 + 1) * 4).astype(np.int64)
+    c_off = np.zeros(N, dtype=np.int64)
+    pos = 0
+    for i in range(N):
+        if pos + mn[i] > c_elems:
+            pos = 0
+        c_off[i] = pos
+        pos += (int(mn[i]) + 63) // 64 * 64
+    a_base, c_base = a_pool.data_ptr(), c_pool.data_ptr()
+
+    def requests(arrivals):
+        arr = (tsmm.Request * N)()
+        for i in range(N):
+            m = int(ms[i])
+            arr[i] = tsmm.Request(i, packed[b_idx[i]].handle, m, 1.0, 0.0, a_base + 4 * int(a_off[i]), m,
+                                  c_base + 4 * int(c_off[i]), m, float(arrivals[i]))
+        return arr
+
+    budget = 40 << 30
+    srv = tsmm.Server(budget_bytes=budget, num_streams=4, max_batch=48, arena_bytes=1 << 30)
+
+    def session(arrivals):
+        arr = requests(arrivals)
+        srv.submit_raw(arr, N)
+        srv.drain(3600.0)
+        comps = srv.poll(N + 16)
+        assert len(comps) == N and all(c["status"] == 0 for c in comps), "serving errors"
+        return comps
+
+    # warm-up (module load, kernel attributes), then capacity with all requests at once
+    session(np.full(N, tsmm.tsmm_server_clock()))
+    t0 = tsmm.tsmm_server_clock() + 0.01
+    comps = session(np.full(N, t0))
+    makespan = max(c["complete_s"] for c in comps) - t0
+    capacity = N / makespan
+    cap_gflops = fl.sum() / makespan / 1e9
+    # open loop: Poisson arrivals at load x capacity
+    lam = args.load * capacity
+    gaps = rng.exponential(1.0 / lam, N)
+    t0 = tsmm.tsmm_server_clock() + 0.05
+    arrivals = t0 + np.cumsum(gaps)
+    comps = session(arrivals)
+    lat = np.array([c["complete_s"] - c["arrival_s"] for c in comps])
+    qwait = np.array([c["admit_s"] - c["arrival_s"] for c in comps])
+    span = max(c["complete_s"] for c in comps) - min(c["arrival_s"] for c in comps)
+    srv.close()
+    line = {"metric": METRIC, "value": round(fl.sum() / span / 1e9, 1), "unit": UNIT, "n_gpus": 1,
+            "steps": 1, "warmup": 1, "ms_per_step": round(span * 1e3, 2), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"serving: {N} FP32 TSMM requests, Poisson arrivals at "
+                                   f"{args.load:.2f} x measured capacity, m log-uniform [1024, 262144], "
+                                   "32 resident packed B with k log-uniform [64, 8192], n log-uniform "
+                                   "[1, 64]; 40 GB admission budget; grouped persistent launches on 4 streams",
+                       "total_gflop": round(fl.sum() / 1e9, 1)},
+            "latency_ms": {"p50": round(float(np.percentile(lat, 50)) * 1e3, 3),
+                           "p90": round(float(np.percentile(lat, 90)) * 1e3, 3),
+                           "p99": round(float(np.percentile(lat, 99)) * 1e3, 3),
+                           "mean": round(float(lat.mean()) * 1e3, 3),
+                           "queue_wait_p99": round(float(np.percentile(qwait, 99)) * 1e3, 3)},
+            "capacity": {"requests_per_s": round(capacity, 1), "gflops": round(cap_gflops, 1),
+                         "makespan_ms": round(makespan * 1e3, 2)},
+            "arrival_rate_per_s": round(lam, 1)}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     args = parse()
+    if args.workload == "serving" and args.impl != "reference":
+        return run_serving(args)
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "precision":

@@ -278,6 +278,66 @@ TSMM_API tsmm_status tsmm_plan_cache_save(const char *path);
 TSMM_API tsmm_status tsmm_plan_cache_clear(void);
 TSMM_API int64_t tsmm_plan_cache_size(void);
 
+/*
+ * Serving runtime: a request loop with continuous batching against
+ * device-resident packed B matrices (the reuse that pre-packing pays for,
+ * Section III).  A scheduler thread owned by the server releases submitted
+ * requests once their arrival time (on the tsmm_server_clock clock) has
+ * passed, admits them in arrival order while the device memory that admitted,
+ * unfinished requests pin -- A (m x k), C (m x n) and the split-K workspace --
+ * stays within budget_bytes, and launches every group of admitted requests
+ * with tsmm_execute_grouped on one of num_streams streams as soon as a stream
+ * is free: requests admitted while earlier batches run form the next batch and
+ * overlap with them on the device.  Completion is detected with CUDA events.
+ * Each request's plan depends only on its shape, so its result is the same bit
+ * for bit alone or in any mix.  The caller owns A, C and the packed B, and must
+ * keep them alive until the request's completion has been polled.
+ */
+typedef struct tsmm_server_s *tsmm_server_t;
+
+typedef struct tsmm_server_config {
+    size_t budget_bytes;  /* device memory admitted, unfinished requests may pin (> 0) */
+    size_t arena_bytes;   /* split-K workspace arena allocated once (0 = 256 MiB); a request's
+                             workspace is capped at a quarter of it */
+    int num_streams;      /* batches that may run concurrently, 1..16 */
+    int max_batch;        /* requests per launch group, 1..1024 */
+    tsmm_dtype dtype;     /* every request's dtype */
+} tsmm_server_config;
+
+typedef struct tsmm_request {
+    uint64_t id;          /* caller's tag, returned with the completion */
+    tsmm_packed_b pb;     /* packed B (native precision, the server's dtype and device) */
+    int64_t m;            /* rows of A and C; k and n come from pb */
+    double alpha, beta;
+    const void *A_dev;    /* m x k, column-major, lda >= max(1, m) */
+    int64_t lda;
+    void *C_dev;          /* m x n, column-major, ldc >= max(1, m); C0 on input */
+    int64_t ldc;
+    double arrival_s;     /* arrival time on tsmm_server_clock(); may be in the future */
+} tsmm_request;
+
+typedef struct tsmm_completion {
+    uint64_t id;
+    double arrival_s, admit_s, launch_s, complete_s; /* tsmm_server_clock() times */
+    int status;                                      /* tsmm_status of the request */
+} tsmm_completion;
+
+/* Create a server on the current device (allocates its arena, streams, events). */
+TSMM_API tsmm_status tsmm_server_create(const tsmm_server_config *cfg, tsmm_server_t *out);
+/* Queue requests (thread-safe).  INVALID_ARG for a request that could never be
+   admitted (its bytes exceed the budget) or has bad arguments; none of the
+   requests of a failing call is queued. */
+TSMM_API tsmm_status tsmm_server_submit(tsmm_server_t s, const tsmm_request *reqs, int count);
+/* Wait until every submitted request has completed (TIMEOUT after timeout_s seconds). */
+TSMM_API tsmm_status tsmm_server_drain(tsmm_server_t s, double timeout_s);
+/* Move up to max completions into out; returns how many. */
+TSMM_API int64_t tsmm_server_poll(tsmm_server_t s, tsmm_completion *out, int64_t max);
+/* Stop the scheduler (requests not yet admitted are dropped), wait for the
+   admitted ones, free everything. */
+TSMM_API tsmm_status tsmm_server_destroy(tsmm_server_t s);
+/* The server's clock: steady, in seconds. */
+TSMM_API double tsmm_server_clock(void);
+
 /* Size of the library's built-in device scratch used by tsmm_execute_noalloc. */
 #define TSMM_NOALLOC_SCRATCH_BYTES (32u << 20)
 

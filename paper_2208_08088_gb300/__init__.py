@@ -32,6 +32,7 @@ __all__ = [
     "tsmm_plan_check", "tsmm_plan_launches_per_execute", "tsmm_autotune",
     "tsmm_plan_cache_load", "tsmm_plan_cache_save", "tsmm_plan_cache_clear", "tsmm_plan_cache_size",
     "autotune", "execute_grouped", "tsmm_execute_grouped", "GroupItem",
+    "Server", "ServerConfig", "Request", "Completion", "tsmm_server_clock",
     "PackedB", "Plan", "pack_b", "plan", "execute", "colmajor", "ld_of",
 ]
 
@@ -57,6 +58,26 @@ class GroupItem(ctypes.Structure):
     _fields_ = [("plan", ctypes.c_void_p), ("alpha", ctypes.c_double), ("A_dev", ctypes.c_void_p),
                 ("lda", ctypes.c_int64), ("pb", ctypes.c_void_p), ("beta", ctypes.c_double),
                 ("C_dev", ctypes.c_void_p), ("ldc", ctypes.c_int64)]
+
+
+class ServerConfig(ctypes.Structure):
+    """struct tsmm_server_config."""
+    _fields_ = [("budget_bytes", ctypes.c_size_t), ("arena_bytes", ctypes.c_size_t),
+                ("num_streams", ctypes.c_int), ("max_batch", ctypes.c_int), ("dtype", ctypes.c_int)]
+
+
+class Request(ctypes.Structure):
+    """struct tsmm_request."""
+    _fields_ = [("id", ctypes.c_uint64), ("pb", ctypes.c_void_p), ("m", ctypes.c_int64),
+                ("alpha", ctypes.c_double), ("beta", ctypes.c_double), ("A_dev", ctypes.c_void_p),
+                ("lda", ctypes.c_int64), ("C_dev", ctypes.c_void_p), ("ldc", ctypes.c_int64),
+                ("arrival_s", ctypes.c_double)]
+
+
+class Completion(ctypes.Structure):
+    """struct tsmm_completion."""
+    _fields_ = [("id", ctypes.c_uint64), ("arrival_s", ctypes.c_double), ("admit_s", ctypes.c_double),
+                ("launch_s", ctypes.c_double), ("complete_s", ctypes.c_double), ("status", ctypes.c_int)]
 
 
 def _load():
@@ -98,6 +119,18 @@ def _load():
     L.tsmm_plan_launches_per_execute.argtypes = [vp]
     L.tsmm_execute_grouped.restype = ci
     L.tsmm_execute_grouped.argtypes = [ctypes.POINTER(GroupItem), ci, vp]
+    L.tsmm_server_create.restype = ci
+    L.tsmm_server_create.argtypes = [ctypes.POINTER(ServerConfig), ctypes.POINTER(vp)]
+    L.tsmm_server_submit.restype = ci
+    L.tsmm_server_submit.argtypes = [vp, ctypes.POINTER(Request), ci]
+    L.tsmm_server_drain.restype = ci
+    L.tsmm_server_drain.argtypes = [vp, dbl]
+    L.tsmm_server_poll.restype = i64
+    L.tsmm_server_poll.argtypes = [vp, ctypes.POINTER(Completion), i64]
+    L.tsmm_server_destroy.restype = ci
+    L.tsmm_server_destroy.argtypes = [vp]
+    L.tsmm_server_clock.restype = dbl
+    L.tsmm_server_clock.argtypes = []
     L.tsmm_autotune.restype = ci
     L.tsmm_autotune.argtypes = [i64, i64, i64, ci, vp, i64, vp, vp, i64, vp, ci, ctypes.POINTER(vp)]
     for name in ("tsmm_plan_cache_load", "tsmm_plan_cache_save"):
@@ -382,3 +415,58 @@ def execute(p: Plan, alpha: float, A, pb: PackedB, beta: float, C, stream=None) 
     tsmm_execute(p.handle, alpha, A.data_ptr() if A.numel() else 0, lda, pb.handle, beta,
                  C.data_ptr() if C.numel() else 0, ld_of(C) if p.n > 0 else max(1, p.m),
                  _stream_handle(stream))
+
+
+# ------------------------------------------------------------------ serving
+def tsmm_server_clock() -> float:
+    return float(lib.tsmm_server_clock())
+
+
+class Server:
+    """Owner of a tsmm_server_t: continuous batching of TSMM requests against
+    device-resident packed B matrices (see include/tsmm.h)."""
+
+    def __init__(self, budget_bytes: int, dtype=F32, num_streams: int = 4, max_batch: int = 48,
+                 arena_bytes: int = 0):
+        dt = dtype if isinstance(dtype, int) else _dtype_code(dtype)
+        cfg = ServerConfig(budget_bytes, arena_bytes, num_streams, max_batch, dt)
+        out = ctypes.c_void_p()
+        _check(lib.tsmm_server_create(ctypes.byref(cfg), ctypes.byref(out)), "tsmm_server_create")
+        self.handle = out.value
+
+    def submit(self, requests) -> None:
+        """requests: sequence of (id, packed_b, m, alpha, A, beta, C, arrival_s) with
+        column-major CUDA tensors A (m x k) and C (m x n)."""
+        arr = (Request * max(1, len(requests)))()
+        for i, (rid, pb, m, alpha, A, beta, C, t) in enumerate(requests):
+            lda = ld_of(A) if m > 0 and A.shape[1] > 0 else max(1, m)
+            ldc = ld_of(C) if m > 0 and C.shape[1] > 0 else max(1, m)
+            arr[i] = Request(rid, pb.handle, m, float(alpha), float(beta),
+                             A.data_ptr() if A.numel() else None, lda,
+                             C.data_ptr() if C.numel() else None, ldc, float(t))
+        _check(lib.tsmm_server_submit(self.handle, arr, len(requests)), "tsmm_server_submit")
+
+    def submit_raw(self, arr, count: int) -> None:
+        """Submit a prepared ctypes array of Request."""
+        _check(lib.tsmm_server_submit(self.handle, arr, count), "tsmm_server_submit")
+
+    def drain(self, timeout_s: float = 600.0) -> None:
+        _check(lib.tsmm_server_drain(self.handle, timeout_s), "tsmm_server_drain")
+
+    def poll(self, max_items: int = 1 << 16):
+        """Completed requests as a list of dicts."""
+        buf = (Completion * max_items)()
+        n = int(lib.tsmm_server_poll(self.handle, buf, max_items))
+        return [dict(id=c.id, arrival_s=c.arrival_s, admit_s=c.admit_s, launch_s=c.launch_s,
+                     complete_s=c.complete_s, status=c.status) for c in buf[:n]]
+
+    def close(self):
+        if self.handle:
+            lib.tsmm_server_destroy(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

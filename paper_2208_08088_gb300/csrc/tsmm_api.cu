@@ -221,7 +221,7 @@ tsmm_status create_plan(int64_t m, int64_t n, int64_t k, tsmm_dtype dtype, int f
     if (!out || !valid_dtype(dtype) || m < 0 || n < 0 || k < 0) return TSMM_ERR_INVALID_ARG;
     const int regime = regime_of(k, n);
     if (regime == 0 || (precision == TSMM_PREC_BF16X3 && regime != 1))
-        return TSMM_ERR_UNSUPPORTED_SHAPE;
+        return TSMM_ERR_UNSUPPORTED_SHAPE;  // before any device query
     const int dev = current_device();
     if (dev < 0) return TSMM_ERR_CUDA;
     int sms = 0;
@@ -230,6 +230,42 @@ tsmm_status create_plan(int64_t m, int64_t n, int64_t k, tsmm_dtype dtype, int f
 
     tsmm_plan_t p = new (std::nothrow) tsmm_plan_s();
     if (!p) return TSMM_ERR_OUT_OF_MEMORY;
+    size_t ticket_bytes = 0;
+    tsmm_status st = plan_layout(m, n, k, dtype, forced_splits, precision, dev, sms, 512LL << 20, p,
+                                 &ticket_bytes);
+    if (st != TSMM_OK) {
+        delete p;
+        return st;
+    }
+    cudaError_t e = cudaSuccess;
+    if (p->workspace_bytes) e = cudaMalloc(&p->workspace, p->workspace_bytes);
+    if (e == cudaSuccess && ticket_bytes) {
+        e = cudaMalloc(reinterpret_cast<void **>(&p->tickets), ticket_bytes);
+        if (e == cudaSuccess) e = cudaMemset(p->tickets, 0, ticket_bytes);
+    }
+    if (e == cudaSuccess) {
+        e = cudaMalloc(reinterpret_cast<void **>(&p->status), sizeof(unsigned));
+        if (e == cudaSuccess) e = cudaMemset(p->status, 0, sizeof(unsigned));
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        if (p->workspace) cudaFree(p->workspace);
+        if (p->tickets) cudaFree(p->tickets);
+        if (p->status) cudaFree(p->status);
+        delete p;
+        return cuda_status(e);
+    }
+    *out = p;
+    return TSMM_OK;
+}
+
+tsmm_status plan_layout(int64_t m, int64_t n, int64_t k, tsmm_dtype dtype, int forced_splits,
+                        int precision, int dev, int sms, int64_t max_workspace, tsmm_plan_s *p,
+                        size_t *ticket_bytes_out) {
+    if (!valid_dtype(dtype) || m < 0 || n < 0 || k < 0) return TSMM_ERR_INVALID_ARG;
+    const int regime = regime_of(k, n);
+    if (regime == 0 || (precision == TSMM_PREC_BF16X3 && regime != 1))
+        return TSMM_ERR_UNSUPPORTED_SHAPE;
     std::memset(static_cast<void *>(p), 0, sizeof(*p));
     p->m = m;
     p->n = n;
@@ -250,7 +286,7 @@ tsmm_status create_plan(int64_t m, int64_t n, int64_t k, tsmm_dtype dtype, int f
         const int64_t kstages = p->kp / kX3KB;
         const int64_t per_split = (int64_t)p->np * p->slabs * p->bm * (int64_t)es;
         int64_t max_splits = 65535;
-        if (per_split > 0) max_splits = std::min<int64_t>(max_splits, (512LL << 20) / per_split);
+        if (per_split > 0) max_splits = std::min<int64_t>(max_splits, max_workspace / per_split);
         int s = (kstages > 0 && p->slabs > 0)
                     ? choose_splits(p->slabs, kstages, sms, max_splits, 1)
                     : 1;
@@ -269,10 +305,10 @@ tsmm_status create_plan(int64_t m, int64_t n, int64_t k, tsmm_dtype dtype, int f
         p->kp = round_up(k, kTallBKS);
         p->slabs = (m + p->bm - 1) / p->bm;
         const int64_t kstages = p->kp / kTallBKS;
-        // keep the workspace within 512 MiB and the grid's y extent legal
+        // keep the workspace within max_workspace and the grid's y extent legal
         const int64_t per_split = (int64_t)p->np * p->slabs * p->bm * (int64_t)es;
         int64_t max_splits = 65535;
-        if (per_split > 0) max_splits = std::min<int64_t>(max_splits, (512LL << 20) / per_split);
+        if (per_split > 0) max_splits = std::min<int64_t>(max_splits, max_workspace / per_split);
         const int per_sm = tall_resident_blocks(dtype == TSMM_F64, p->np);
         int s = (kstages > 0 && p->slabs > 0)
                     ? choose_splits(p->slabs, kstages, sms, max_splits, per_sm)
@@ -294,25 +330,7 @@ tsmm_status create_plan(int64_t m, int64_t n, int64_t k, tsmm_dtype dtype, int f
         p->mtiles = (m + p->bm - 1) / p->bm;
         p->ntiles = (n + kRankNT - 1) / kRankNT;
     }
-    cudaError_t e = cudaSuccess;
-    if (p->workspace_bytes) e = cudaMalloc(&p->workspace, p->workspace_bytes);
-    if (e == cudaSuccess && ticket_bytes) {
-        e = cudaMalloc(reinterpret_cast<void **>(&p->tickets), ticket_bytes);
-        if (e == cudaSuccess) e = cudaMemset(p->tickets, 0, ticket_bytes);
-    }
-    if (e == cudaSuccess) {
-        e = cudaMalloc(reinterpret_cast<void **>(&p->status), sizeof(unsigned));
-        if (e == cudaSuccess) e = cudaMemset(p->status, 0, sizeof(unsigned));
-    }
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        if (p->workspace) cudaFree(p->workspace);
-        if (p->tickets) cudaFree(p->tickets);
-        if (p->status) cudaFree(p->status);
-        delete p;
-        return cuda_status(e);
-    }
-    *out = p;
+    if (ticket_bytes_out) *ticket_bytes_out = ticket_bytes;
     return TSMM_OK;
 }
 

@@ -130,6 +130,13 @@ cudaError_t launch_rankk(tsmm_dtype dt, const CUtensorMap *tmA, const CUtensorMa
 tsmm_status create_plan(int64_t m, int64_t n, int64_t k, tsmm_dtype dtype, int forced_splits,
                         tsmm_plan_t *out, int precision = 0);
 
+// Plan fields without any device allocation: every member except workspace,
+// tickets and status, plus the ticket bytes the plan needs; split-K workspaces
+// are capped at max_workspace bytes.  (Used by create_plan and the server.)
+tsmm_status plan_layout(int64_t m, int64_t n, int64_t k, tsmm_dtype dtype, int forced_splits,
+                        int precision, int dev, int sms, int64_t max_workspace, tsmm_plan_s *p,
+                        size_t *ticket_bytes_out);
+
 // BF16x3 precision mode (tsmm_bf16x3.cu): k granule of its packed B and plan.
 constexpr int kX3KB = 64;
 inline int x3_np(int64_t n) {

@@ -1,0 +1,384 @@
+// Serving runtime: a request loop with continuous batching over device-resident
+// pre-packed B matrices -- the reuse scenario that motivates pre-packing in the
+// paper (Section III: the execution plan and the packed operand are reused by
+// many executions, so their cost is amortised).
+//
+// A scheduler thread owned by the server:
+//   * releases submitted requests when their arrival time has passed;
+//   * admits them in arrival order (FIFO) while the device memory pinned by
+//     admitted, unfinished requests (A + C + split-K workspace) stays within the
+//     budget, and while a workspace slice fits in the server's arena;
+//   * launches the admitted requests as one tsmm_execute_grouped batch on a
+//     free stream as soon as one is free -- requests admitted while other
+//     batches are on the GPU form the next batch, so their work overlaps;
+//   * detects batch completion with CUDA events, records completion times and
+//     returns the batch's memory to the budget and the arena.
+// Results are deterministic: each request's plan depends only on its shape,
+// never on what else is in flight.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <vector>
+
+#include "tsmm_device.cuh"
+#include "tsmm_internal.h"
+
+using namespace tsmm;
+
+namespace {
+
+double now_s() {
+    using clk = std::chrono::steady_clock;
+    return std::chrono::duration<double>(clk::now().time_since_epoch()).count();
+}
+
+// First-fit allocator over one device buffer (offsets aligned to 256 bytes).
+struct Arena {
+    size_t size = 0;
+    std::map<size_t, size_t> free_;  // offset -> bytes
+    void init(size_t bytes) {
+        size = bytes;
+        free_.clear();
+        if (bytes) free_[0] = bytes;
+    }
+    bool alloc(size_t bytes, size_t *off) {
+        bytes = (bytes + 255) / 256 * 256;
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second >= bytes) {
+                *off = it->first;
+                const size_t rest = it->second - bytes;
+                const size_t start = it->first + bytes;
+                free_.erase(it);
+                if (rest) free_[start] = rest;
+                return true;
+            }
+        }
+        return false;
+    }
+    void release(size_t off, size_t bytes) {
+        bytes = (bytes + 255) / 256 * 256;
+        auto it = free_.emplace(off, bytes).first;
+        auto next = std::next(it);
+        if (next != free_.end() && it->first + it->second == next->first) {
+            it->second += next->second;
+            free_.erase(next);
+        }
+        if (it != free_.begin()) {
+            auto prev = std::prev(it);
+            if (prev->first + prev->second == it->first) {
+                prev->second += it->second;
+                free_.erase(it);
+            }
+        }
+    }
+};
+
+struct Req {
+    tsmm_request r;
+    tsmm_plan_s plan;
+    size_t ticket_bytes = 0;
+    size_t bytes = 0;  // budget charge: A + C + workspace
+    size_t ws_off = 0, tk_off = 0;
+    double admit_s = 0, launch_s = 0;
+};
+
+struct Batch {
+    std::vector<Req *> reqs;
+    cudaEvent_t ev = nullptr;
+    int stream = -1;
+};
+
+}  // namespace
+
+struct tsmm_server_s {
+    tsmm_server_config cfg;
+    int dev = 0, sms = 0;
+    std::vector<cudaStream_t> streams;
+    std::vector<char> stream_busy;
+    std::vector<cudaEvent_t> events;  // one per stream
+    void *ws_base = nullptr;
+    void *tk_base = nullptr;
+    unsigned *status_host = nullptr;  // mapped, pinned
+    unsigned *status_dev = nullptr;   // its device address
+    Arena ws_arena, tk_arena;
+
+    std::mutex mu;
+    std::condition_variable cv_done;
+    std::multimap<double, Req *> pending;  // submitted, keyed by arrival time
+    std::deque<tsmm_completion> completions;
+    int64_t submitted = 0, completed = 0;
+    tsmm_status fault = TSMM_OK;
+
+    // scheduler-thread state
+    std::deque<Req *> ready;
+    std::vector<Req *> forming;
+    std::vector<Batch> inflight;
+    size_t inflight_bytes = 0;
+    std::atomic<bool> stop{false};
+    std::thread th;
+
+    void run();
+    bool try_admit(Req *q, double t);
+    void launch(double t);
+    bool poll_batches();
+    void finish(Batch &b, int status, double t);
+};
+
+bool tsmm_server_s::try_admit(Req *q, double t) {
+    if (inflight_bytes + q->bytes > cfg.budget_bytes) return false;
+    if (q->plan.workspace_bytes && !ws_arena.alloc(q->plan.workspace_bytes, &q->ws_off)) return false;
+    if (q->ticket_bytes && !tk_arena.alloc(q->ticket_bytes, &q->tk_off)) {
+        if (q->plan.workspace_bytes) ws_arena.release(q->ws_off, q->plan.workspace_bytes);
+        return false;
+    }
+    q->plan.workspace = q->plan.workspace_bytes ? static_cast<char *>(ws_base) + q->ws_off : nullptr;
+    q->plan.tickets = q->ticket_bytes
+                          ? reinterpret_cast<unsigned *>(static_cast<char *>(tk_base) + q->tk_off)
+                          : nullptr;
+    q->plan.status = status_dev;
+    q->admit_s = t;
+    inflight_bytes += q->bytes;
+    return true;
+}
+
+void tsmm_server_s::launch(double t) {
+    int s = -1;
+    for (int i = 0; i < (int)streams.size(); ++i)
+        if (!stream_busy[i]) {
+            s = i;
+            break;
+        }
+    if (s < 0 || forming.empty()) return;
+    std::vector<tsmm_group_item> items(forming.size());
+    for (size_t i = 0; i < forming.size(); ++i) {
+        const tsmm_request &r = forming[i]->r;
+        items[i] = tsmm_group_item{&forming[i]->plan, r.alpha, r.A_dev, r.lda, r.pb, r.beta, r.C_dev,
+                                   r.ldc};
+        forming[i]->launch_s = t;
+    }
+    Batch b;
+    b.reqs = forming;
+    b.stream = s;
+    b.ev = events[s];
+    forming.clear();
+    tsmm_status st = tsmm_execute_grouped(items.data(), (int)items.size(), streams[s]);
+    if (st == TSMM_OK && cudaEventRecord(b.ev, streams[s]) != cudaSuccess) st = TSMM_ERR_CUDA;
+    if (st != TSMM_OK) {
+        finish(b, st, now_s());
+        return;
+    }
+    stream_busy[s] = 1;
+    inflight.push_back(std::move(b));
+}
+
+void tsmm_server_s::finish(Batch &b, int status, double t) {
+    std::lock_guard<std::mutex> lock(mu);
+    for (Req *q : b.reqs) {
+        inflight_bytes -= q->bytes;
+        if (q->plan.workspace_bytes) ws_arena.release(q->ws_off, q->plan.workspace_bytes);
+        if (q->ticket_bytes) tk_arena.release(q->tk_off, q->ticket_bytes);
+        completions.push_back(
+            tsmm_completion{q->r.id, q->r.arrival_s, q->admit_s, q->launch_s, t, status});
+        delete q;
+        ++completed;
+    }
+    if (b.stream >= 0) stream_busy[b.stream] = 0;
+    cv_done.notify_all();
+}
+
+bool tsmm_server_s::poll_batches() {
+    bool progress = false;
+    for (size_t i = 0; i < inflight.size();) {
+        cudaError_t e = cudaEventQuery(inflight[i].ev);
+        if (e == cudaErrorNotReady) {
+            ++i;
+            continue;
+        }
+        int status = e == cudaSuccess ? TSMM_OK : TSMM_ERR_CUDA;
+        // the kernels' give-up record lives in mapped host memory: read it directly
+        if (e == cudaSuccess && *reinterpret_cast<volatile unsigned *>(status_host) != 0u) {
+            status = TSMM_ERR_TIMEOUT;
+            *reinterpret_cast<volatile unsigned *>(status_host) = 0u;
+        }
+        Batch b = std::move(inflight[i]);
+        inflight.erase(inflight.begin() + i);
+        finish(b, status, now_s());
+        progress = true;
+    }
+    return progress;
+}
+
+void tsmm_server_s::run() {
+    cudaSetDevice(dev);
+    for (;;) {
+        bool progress = false;
+        const double t = now_s();
+        {
+            std::lock_guard<std::mutex> lock(mu);
+            while (!pending.empty() && pending.begin()->first <= t) {
+                ready.push_back(pending.begin()->second);
+                pending.erase(pending.begin());
+                progress = true;
+            }
+        }
+        // admission in arrival order while memory allows; batch what was admitted
+        while (!stop.load() && !ready.empty() && (int)forming.size() < cfg.max_batch) {
+            if (!try_admit(ready.front(), t)) break;
+            forming.push_back(ready.front());
+            ready.pop_front();
+            progress = true;
+        }
+        if (!forming.empty()) {
+            const size_t before = inflight.size();
+            launch(t);
+            progress |= inflight.size() != before;
+        }
+        progress |= poll_batches();
+        // on shutdown, requests not yet admitted are dropped; admitted ones finish
+        if (stop.load() && forming.empty() && inflight.empty()) break;
+        if (!progress) std::this_thread::sleep_for(std::chrono::microseconds(20));
+    }
+}
+
+extern "C" {
+
+double tsmm_server_clock(void) { return now_s(); }
+
+tsmm_status tsmm_server_create(const tsmm_server_config *cfg, tsmm_server_t *out) {
+    if (!cfg || !out) return TSMM_ERR_INVALID_ARG;
+    if ((cfg->dtype != TSMM_F32 && cfg->dtype != TSMM_F64) || cfg->budget_bytes == 0 ||
+        cfg->num_streams < 1 || cfg->num_streams > 16 || cfg->max_batch < 1 || cfg->max_batch > 1024)
+        return TSMM_ERR_INVALID_ARG;
+    tsmm_server_t s = new (std::nothrow) tsmm_server_s();
+    if (!s) return TSMM_ERR_OUT_OF_MEMORY;
+    s->cfg = *cfg;
+    if (s->cfg.arena_bytes == 0) s->cfg.arena_bytes = 256u << 20;
+    cudaError_t e = cudaGetDevice(&s->dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, s->dev);
+    const size_t tk_bytes = 16u << 20;
+    if (e == cudaSuccess) e = cudaMalloc(&s->ws_base, s->cfg.arena_bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&s->tk_base, tk_bytes);
+    if (e == cudaSuccess) e = cudaMemset(s->tk_base, 0, tk_bytes);  // arrival counters start at 0
+    if (e == cudaSuccess)
+        e = cudaHostAlloc(reinterpret_cast<void **>(&s->status_host), sizeof(unsigned), cudaHostAllocMapped);
+    if (e == cudaSuccess) {
+        *s->status_host = 0u;
+        e = cudaHostGetDevicePointer(reinterpret_cast<void **>(&s->status_dev), s->status_host, 0);
+    }
+    for (int i = 0; e == cudaSuccess && i < cfg->num_streams; ++i) {
+        cudaStream_t st;
+        cudaEvent_t ev;
+        e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+        if (e == cudaSuccess) {
+            s->streams.push_back(st);
+            e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+            if (e == cudaSuccess) s->events.push_back(ev);
+        }
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        for (auto st : s->streams) cudaStreamDestroy(st);
+        for (auto ev : s->events) cudaEventDestroy(ev);
+        if (s->ws_base) cudaFree(s->ws_base);
+        if (s->tk_base) cudaFree(s->tk_base);
+        if (s->status_host) cudaFreeHost(s->status_host);
+        delete s;
+        return e == cudaErrorMemoryAllocation ? TSMM_ERR_OUT_OF_MEMORY : TSMM_ERR_CUDA;
+    }
+    s->stream_busy.assign(s->streams.size(), 0);
+    s->ws_arena.init(s->cfg.arena_bytes);
+    s->tk_arena.init(tk_bytes);
+    s->th = std::thread([s] { s->run(); });
+    *out = s;
+    return TSMM_OK;
+}
+
+tsmm_status tsmm_server_submit(tsmm_server_t s, const tsmm_request *reqs, int count) {
+    if (!s || count < 0 || (count > 0 && !reqs)) return TSMM_ERR_INVALID_ARG;
+    std::vector<Req *> made;
+    made.reserve(count);
+    tsmm_status st = TSMM_OK;
+    for (int i = 0; i < count && st == TSMM_OK; ++i) {
+        const tsmm_request &r = reqs[i];
+        tsmm_packed_b pb = r.pb;
+        if (!pb || pb->dtype != s->cfg.dtype || pb->precision != TSMM_PREC_NATIVE || r.m < 0 ||
+            r.lda < std::max<int64_t>(1, r.m) || r.ldc < std::max<int64_t>(1, r.m) ||
+            (r.m > 0 && pb->n > 0 && !r.C_dev) || (r.m > 0 && pb->k > 0 && r.alpha != 0.0 && !r.A_dev)) {
+            st = TSMM_ERR_INVALID_ARG;
+            break;
+        }
+        if (pb->device != s->dev) {
+            st = TSMM_ERR_MISMATCH;
+            break;
+        }
+        Req *q = new (std::nothrow) Req();
+        if (!q) {
+            st = TSMM_ERR_OUT_OF_MEMORY;
+            break;
+        }
+        q->r = r;
+        const int cached = plan_cache_lookup(s->cfg.dtype, r.m, pb->n, pb->k, s->sms);
+        st = plan_layout(r.m, pb->n, pb->k, s->cfg.dtype, cached, TSMM_PREC_NATIVE, s->dev, s->sms,
+                         (int64_t)(s->cfg.arena_bytes / 4), &q->plan, &q->ticket_bytes);
+        const size_t es = dtype_size(s->cfg.dtype);
+        q->bytes = es * (size_t)r.m * (size_t)(pb->k + pb->n) + q->plan.workspace_bytes;
+        if (st == TSMM_OK && (q->bytes > s->cfg.budget_bytes || q->ticket_bytes > (16u << 20)))
+            st = TSMM_ERR_INVALID_ARG;  // could never be admitted
+        if (st != TSMM_OK) {
+            delete q;
+            break;
+        }
+        made.push_back(q);
+    }
+    if (st != TSMM_OK) {
+        for (Req *q : made) delete q;
+        return st;
+    }
+    std::lock_guard<std::mutex> lock(s->mu);
+    for (Req *q : made) s->pending.emplace(q->r.arrival_s, q);
+    s->submitted += (int64_t)made.size();
+    return TSMM_OK;
+}
+
+int64_t tsmm_server_poll(tsmm_server_t s, tsmm_completion *out, int64_t max) {
+    if (!s || !out || max <= 0) return 0;
+    std::lock_guard<std::mutex> lock(s->mu);
+    int64_t n = 0;
+    while (n < max && !s->completions.empty()) {
+        out[n++] = s->completions.front();
+        s->completions.pop_front();
+    }
+    return n;
+}
+
+tsmm_status tsmm_server_drain(tsmm_server_t s, double timeout_s) {
+    if (!s) return TSMM_ERR_INVALID_ARG;
+    std::unique_lock<std::mutex> lock(s->mu);
+    const bool ok = s->cv_done.wait_for(lock, std::chrono::duration<double>(timeout_s),
+                                        [s] { return s->completed >= s->submitted; });
+    return ok ? TSMM_OK : TSMM_ERR_TIMEOUT;
+}
+
+tsmm_status tsmm_server_destroy(tsmm_server_t s) {
+    if (!s) return TSMM_OK;
+    s->stop.store(true);
+    if (s->th.joinable()) s->th.join();
+    for (auto st : s->streams) cudaStreamSynchronize(st);
+    for (auto &kv : s->pending) delete kv.second;
+    for (Req *q : s->ready) delete q;
+    for (auto st : s->streams) cudaStreamDestroy(st);
+    for (auto ev : s->events) cudaEventDestroy(ev);
+    cudaFree(s->ws_base);
+    cudaFree(s->tk_base);
+    cudaFreeHost(s->status_host);
+    delete s;
+    return TSMM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,118 @@
+"""Serving runtime: continuous batching of TSMM requests against device-resident
+packed B matrices.  Every result must be the same, bit for bit, whether the
+request ran alone or in the mix (its plan depends only on its shape), and
+within the oracle's bound; admission must respect the memory budget; batches
+must overlap on the device."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2208_08088_gb300 as tsmm
+import tsmm_inputs as ti
+from gpu_util import to_device
+
+pytestmark = pytest.mark.gpu
+
+B_SPECS = [(64, 1), (200, 16), (777, 64), (1500, 8), (4000, 33), (100, 3)]
+
+
+def make_bs(dtype=np.float32):
+    out = []
+    for i, (k, n) in enumerate(B_SPECS):
+        B = ti.matrix_np(k, n, 500 + i, "uniform", dtype)
+        out.append((k, n, B, tsmm.pack_b(to_device(B))))
+    return out
+
+
+def make_requests(bs, count, seed, dtype=np.float32):
+    rng = np.random.default_rng(seed)
+    reqs = []
+    for rid in range(count):
+        b = int(rng.integers(len(bs)))
+        k, n, B, pb = bs[b]
+        m = int(np.exp(rng.uniform(np.log(100), np.log(8000))))
+        A = ti.matrix_np(m, k, 1000 + rid, "uniform", dtype)
+        C0 = ti.matrix_np(m, n, 2000 + rid, "uniform", dtype)
+        reqs.append(dict(id=rid, b=b, m=m, A=A, C0=C0, alpha=1.5, beta=0.5 if rid % 3 else 0.0))
+    return reqs
+
+
+def run(server, bs, reqs, spread_s=0.0, seed=0):
+    rng = np.random.default_rng(seed)
+    t0 = tsmm.tsmm_server_clock() + 0.002
+    devs, batch = {}, []
+    for q in reqs:
+        k, n, B, pb = bs[q["b"]]
+        dA, dC = to_device(q["A"]), to_device(q["C0"])
+        devs[q["id"]] = (dA, dC)
+        batch.append((q["id"], pb, q["m"], q["alpha"], dA, q["beta"], dC,
+                      t0 + (rng.uniform(0, spread_s) if spread_s else 0.0)))
+    server.submit(batch)
+    server.drain(120.0)
+    comps = {c["id"]: c for c in server.poll()}
+    assert len(comps) == len(reqs) and all(c["status"] == 0 for c in comps.values())
+    return {rid: d[1].cpu().numpy() for rid, d in devs.items()}, comps
+
+
+def test_serving_same_alone_and_in_mix():
+    bs = make_bs()
+    reqs = make_requests(bs, 40, seed=1)
+    # alone: one request at a time through a server
+    alone = {}
+    srv = tsmm.Server(budget_bytes=8 << 30, num_streams=4, max_batch=16)
+    for q in reqs:
+        res, _ = run(srv, bs, [q])
+        alone[q["id"]] = res[q["id"]]
+    srv.close()
+    # in the mix: all of them, arriving over 20 ms, overlapping on the device
+    srv = tsmm.Server(budget_bytes=8 << 30, num_streams=4, max_batch=16)
+    mix, comps = run(srv, bs, reqs, spread_s=0.02, seed=2)
+    srv.close()
+    for q in reqs:
+        assert np.array_equal(mix[q["id"]], alone[q["id"]]), f"request {q['id']} differs"
+        k, n, B, pb = bs[q["b"]]
+        Cref, E = oracle.tsmm(q["alpha"], q["A"], B, q["beta"], q["C0"] if q["beta"] else None)
+        ok, ratio, nbad = oracle.check(mix[q["id"]], Cref, E, np.float32)
+        assert ok, f"request {q['id']}: {nbad} entries outside the bound"
+    for c in comps.values():
+        assert c["arrival_s"] <= c["admit_s"] <= c["launch_s"] <= c["complete_s"]
+
+
+def test_serving_admission_respects_budget_and_batches_overlap():
+    bs = make_bs()
+    reqs = make_requests(bs, 60, seed=3)
+    es = 4
+    sizes = {q["id"]: es * q["m"] * (bs[q["b"]][0] + bs[q["b"]][1]) for q in reqs}
+    budget = 3 * max(sizes.values())
+    srv = tsmm.Server(budget_bytes=budget, num_streams=4, max_batch=8)
+    _, comps = run(srv, bs, reqs, spread_s=0.0, seed=4)
+    srv.close()
+    # at every admission, the requests admitted and not yet completed fit the budget
+    ev = sorted(comps.values(), key=lambda c: c["admit_s"])
+    for c in ev:
+        live = sum(sizes[d["id"]] for d in ev if d["admit_s"] <= c["admit_s"] < d["complete_s"])
+        assert live <= budget
+    # with a roomy budget, admitted work overlaps on the device (several batches in flight)
+    srv = tsmm.Server(budget_bytes=16 << 30, num_streams=4, max_batch=4)
+    _, comps = run(srv, bs, reqs, spread_s=0.0, seed=5)
+    srv.close()
+    spans = sorted((c["launch_s"], c["complete_s"]) for c in comps.values())
+    overlap = max(sum(1 for (a, b) in spans if a <= t < b) for (t, _) in spans)
+    assert overlap >= 2
+
+
+def test_serving_rejects_requests_larger_than_budget():
+    bs = make_bs()
+    k, n, B, pb = bs[2]
+    A = to_device(ti.matrix_np(5000, k, 1, "uniform", np.float32))
+    C = to_device(np.zeros((5000, n), np.float32, order="F"))
+    srv = tsmm.Server(budget_bytes=1 << 20, num_streams=1, max_batch=1)
+    with pytest.raises(tsmm.TsmmError) as e:
+        srv.submit([(0, pb, 5000, 1.0, A, 0.0, C, 0.0)])
+    assert e.value.status == 1
+    # a future request is dropped cleanly when the server is closed before it arrives
+    small = to_device(ti.matrix_np(10, k, 1, "uniform", np.float32))
+    Cs = to_device(np.zeros((10, n), np.float32, order="F"))
+    srv.submit([(1, pb, 10, 1.0, small, 0.0, Cs, tsmm.tsmm_server_clock() + 3600.0)])
+    srv.close()

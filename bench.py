@@ -302,6 +302,22 @@ def recorded_traffic(kernel_key, family):
     return ent.get("dram_bytes_per_launch")
 
 
+def aggregate_over_ranks(elapsed_ms, step_flops, steps, world):
+    """Whole-job throughput of `world` replicas: every rank's flops divided by
+    the slowest rank's time (max over ranks; no collective touches the data).
+    Works with any torch.distributed backend (gloo on CPU in the tests)."""
+    import torch
+    import torch.distributed as dist
+
+    if world > 1:
+        dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+        t = torch.tensor([float(elapsed_ms)], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    value = world * step_flops * steps / (elapsed_ms * 1e-3) / 1e9
+    return elapsed_ms, value
+
+
 def run_ours(args):
     import torch
 
@@ -378,13 +394,8 @@ def run_ours(args):
     elapsed_ms = start.elapsed_time(stop)
     for pl in plans.values():
         pl.check()
-    if world > 1:
-        t = torch.tensor([elapsed_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
-
     step_flops = sum(flops(m, n, k) for (m, n, k, _) in pts)
-    value = world * step_flops * args.steps / (elapsed_ms * 1e-3) / 1e9
+    elapsed_ms, value = aggregate_over_ranks(elapsed_ms, step_flops, args.steps, world)
     launches = args.steps * sum(plans[(m, n, k)].launches_per_execute() for (m, n, k, _) in pts)
 
     hbm_peak, hbm_src = load_peaks()

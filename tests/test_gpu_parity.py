@@ -264,3 +264,16 @@ def test_rankk_persistent_many_tiles(dtype, k, beta):
     C, pl, _ = run(A, B, C0 if beta != 0 else None, 1.0 if k != 33 else 0.75, beta)
     assert pl.info()["regime"] == 2
     assert_parity(C, A, B, C0 if beta != 0 else None, 1.0 if k != 33 else 0.75, beta)
+
+
+def test_config1_integer_matches_golden_fixture():
+    """GPU rows of the m = k = 2048, n = 16 integer workload equal the committed
+    fixture (written by tests/golden/make_golden.py from the oracle) bit for bit."""
+    import json
+    import os
+    fx = json.load(open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                                     "config1_integer_rows.json")))
+    m, n, k = fx["m"], fx["n"], fx["k"]
+    A, B, C0 = gen(m, n, k, np.float32, "integer")
+    C, _, _ = run(A, B, C0, fx["alpha"], fx["beta"])
+    np.testing.assert_array_equal(C[fx["rows"]], np.array(fx["C_rows"], dtype=np.float32))

@@ -349,3 +349,19 @@ def test_check_semantics():
     assert ok and abs(ratio - 0.8) < 1e-12
     ok, _, nbad = oracle.check(np.array([[1.6, 2.0, np.nan, np.inf, 0.1]]), Cref, E, np.float32)
     assert not ok and nbad == 2  # 1.6 out of bound; 0.1 (double) != fl32(0.1)
+
+
+def test_golden_fixture_reproduces():
+    """The committed fixture equals what its generator script computes now
+    (exact integers: any change in the oracle's arithmetic would show)."""
+    import json
+    import importlib.util
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    path = os.path.join(root, "tests", "golden", "make_golden.py")
+    spec = importlib.util.spec_from_file_location("make_golden", path)
+    mg = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mg)
+    stored = json.load(open(os.path.join(root, "tests", "golden", "config1_integer_rows.json")))
+    assert mg.config1_integer() == stored
+    # and the stored values are integers / 2 (alpha = 1.5, beta = 0.5 on integers)
+    assert all(float(2 * x).is_integer() for row in stored["C_rows"] for x in row)

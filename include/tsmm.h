@@ -74,7 +74,7 @@ typedef enum {
 
 /*
  * Arithmetic of a plan / packed B.  NATIVE: IEEE fma in the working precision
- * (the contract stated above).  BF16X3 (TSMM_F32, regime (i) only): the
+ * (the contract stated above).  BF16X3 (TSMM_F32, both regimes): the
  * tensor-core mode C = alpha*(A_hi*B_hi + A_hi*B_lo + A_lo*B_hi) + beta*C0
  * with x_hi = bf16(x), x_lo = bf16(x - x_hi) and FP32 accumulation in tensor
  * memory (tcgen05.mma).  It drops A_lo*B_lo and the split residues, about
@@ -95,6 +95,11 @@ TSMM_API const char *tsmm_status_string(tsmm_status status);
 
 /* Library version as major*10000 + minor*100 + patch. */
 TSMM_API int tsmm_version(void);
+
+/* The CUDA runtime's message for the last CUDA failure that one of this
+   thread's calls turned into TSMM_ERR_CUDA / TSMM_ERR_OUT_OF_MEMORY (static
+   string, never NULL; "no error" before any). */
+TSMM_API const char *tsmm_last_cuda_error(void);
 
 /*
  * tsmm_pack_b -- PACKB of Algorithm 1: copy B (k x n, column-major, leading
@@ -122,12 +127,13 @@ TSMM_API tsmm_status tsmm_pack_b(tsmm_dtype dtype, int64_t k, int64_t n, const v
 
 /*
  * tsmm_pack_b_ex -- tsmm_pack_b with an explicit precision mode.  BF16X3 packs
- * B once as hi and lo BF16 copies in the tensor-core operand layout: per
- * 64-row chunk c of k (kp = k rounded up to 64), a hi tile then a lo tile, each
- * w x 64 BF16 values (w = n rounded up to a power of two, at least 16), element
- * (column j, row kk) at byte (j/8)*1024 + (kk/8)*128 + (j%8)*16 + (kk%8)*2 of
- * the tile.  INVALID_ARG for BF16X3 with TSMM_F64; UNSUPPORTED_SHAPE for
- * BF16X3 with n > 64.
+ * B once as hi and lo BF16 copies in the tensor-core operand layout: the
+ * columns are cut into `ntiles` tiles of w columns (regime (i): one tile, w = n
+ * rounded up to a power of two, at least 16; regime (ii): w = 128); per tile and
+ * per 64-row chunk c of k (kp = k rounded up to 64), a hi tile then a lo tile,
+ * each w x 64 BF16 values, element (column j, row kk) at byte (j/8)*1024 +
+ * (kk/8)*128 + (j%8)*16 + (kk%8)*2 of the tile; chunk c of tile t starts at byte
+ * (t*kp/64 + c) * 4*w*64.  INVALID_ARG for BF16X3 with TSMM_F64.
  */
 TSMM_API tsmm_status tsmm_pack_b_ex(tsmm_dtype dtype, tsmm_precision precision, int64_t k, int64_t n,
                                     const void *B_dev, int64_t ldb, tsmm_stream_t stream,

@@ -48,9 +48,9 @@ library_path = _build.LIB
 
 
 class TsmmError(RuntimeError):
-    def __init__(self, status: int, where: str):
+    def __init__(self, status: int, where: str, detail: str = ""):
         self.status = status
-        super().__init__(f"{where}: {STATUS.get(status, status)}")
+        super().__init__(f"{where}: {STATUS.get(status, status)}" + (f" ({detail})" if detail else ""))
 
 
 class GroupItem(ctypes.Structure):
@@ -92,6 +92,8 @@ def _load():
     L.tsmm_status_string.argtypes = [ci]
     L.tsmm_version.restype = ci
     L.tsmm_version.argtypes = []
+    L.tsmm_last_cuda_error.restype = ctypes.c_char_p
+    L.tsmm_last_cuda_error.argtypes = []
     L.tsmm_pack_b.restype = ci
     L.tsmm_pack_b.argtypes = [ci, i64, i64, vp, i64, vp, ctypes.POINTER(vp)]
     L.tsmm_pack_b_ex.restype = ci
@@ -148,7 +150,8 @@ lib = _load()
 
 def _check(status: int, where: str):
     if status != 0:
-        raise TsmmError(status, where)
+        detail = lib.tsmm_last_cuda_error().decode() if status in (5, 6) else ""
+        raise TsmmError(status, where, detail)
 
 
 # ------------------------------------------------------------------ C ABI names

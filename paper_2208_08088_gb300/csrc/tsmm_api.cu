@@ -37,8 +37,11 @@ bool valid_dtype(tsmm_dtype d) { return d == TSMM_F32 || d == TSMM_F64; }
 
 bool aligned(const void *p, size_t a) { return reinterpret_cast<uintptr_t>(p) % a == 0; }
 
+thread_local const char *g_last_cuda_error = "no error";
+
 tsmm_status cuda_status(cudaError_t e) {
     if (e == cudaSuccess) return TSMM_OK;
+    g_last_cuda_error = cudaGetErrorString(e);  // static string owned by the runtime
     if (e == cudaErrorMemoryAllocation) return TSMM_ERR_OUT_OF_MEMORY;
     return TSMM_ERR_CUDA;
 }
@@ -97,6 +100,8 @@ const char *tsmm_status_string(tsmm_status status) {
 
 int tsmm_version(void) { return kVersion; }
 
+const char *tsmm_last_cuda_error(void) { return g_last_cuda_error; }
+
 tsmm_status tsmm_pack_b(tsmm_dtype dtype, int64_t k, int64_t n, const void *B_dev, int64_t ldb,
                         tsmm_stream_t stream, tsmm_packed_b *out) {
     return tsmm_pack_b_ex(dtype, TSMM_PREC_NATIVE, k, n, B_dev, ldb, stream, out);
@@ -112,8 +117,7 @@ tsmm_status tsmm_pack_b_ex(tsmm_dtype dtype, tsmm_precision precision, int64_t k
     const size_t es = dtype_size(dtype);
     if (B_dev && !aligned(B_dev, es)) return TSMM_ERR_MISALIGNED;
     const int regime = regime_of(k, n);
-    if (regime == 0 || (precision == TSMM_PREC_BF16X3 && regime != 1))
-        return TSMM_ERR_UNSUPPORTED_SHAPE;
+    if (regime == 0) return TSMM_ERR_UNSUPPORTED_SHAPE;
     const int dev = current_device();
     if (dev < 0) return TSMM_ERR_CUDA;
 
@@ -127,8 +131,8 @@ tsmm_status tsmm_pack_b_ex(tsmm_dtype dtype, tsmm_precision precision, int64_t k
     pb->device = dev;
     if (precision == TSMM_PREC_BF16X3) {
         pb->kp = round_up(k, kX3KB);
-        pb->w = x3_np(n);
-        pb->ntiles = 1;
+        pb->w = regime == 1 ? x3_np(n) : kX3RankNT;
+        pb->ntiles = regime == 1 ? 1 : (n + kX3RankNT - 1) / kX3RankNT;
     } else if (regime == 1) {
         pb->kp = round_up(k, kTallBKS);
         pb->w = tall_np(n);
@@ -139,7 +143,7 @@ tsmm_status tsmm_pack_b_ex(tsmm_dtype dtype, tsmm_precision precision, int64_t k
         pb->ntiles = (n + kRankNT - 1) / kRankNT;
     }
     // BF16x3: a hi and a lo BF16 copy of every element
-    pb->bytes = precision == TSMM_PREC_BF16X3 ? (size_t)(pb->kp * pb->w) * 2 * 2
+    pb->bytes = precision == TSMM_PREC_BF16X3 ? (size_t)(pb->kp * pb->w * pb->ntiles) * 2 * 2
                                               : (size_t)(pb->kp * pb->w * pb->ntiles) * es;
     pb->data = nullptr;
     if (pb->bytes > 0) {
@@ -151,7 +155,7 @@ tsmm_status tsmm_pack_b_ex(tsmm_dtype dtype, tsmm_precision precision, int64_t k
         }
         e = precision == TSMM_PREC_BF16X3
                 ? launch_pack_b_bf16x3(k, n, B_dev, ldb, pb->data, (int)pb->w, pb->kp / kX3KB,
-                                       static_cast<cudaStream_t>(stream))
+                                       pb->ntiles, static_cast<cudaStream_t>(stream))
                 : launch_pack_b(dtype, k, n, B_dev, ldb, pb->data, pb->kp, pb->w, pb->ntiles,
                                 static_cast<cudaStream_t>(stream));
         if (e != cudaSuccess) {
@@ -220,8 +224,7 @@ tsmm_status create_plan(int64_t m, int64_t n, int64_t k, tsmm_dtype dtype, int f
                         tsmm_plan_t *out, int precision) {
     if (!out || !valid_dtype(dtype) || m < 0 || n < 0 || k < 0) return TSMM_ERR_INVALID_ARG;
     const int regime = regime_of(k, n);
-    if (regime == 0 || (precision == TSMM_PREC_BF16X3 && regime != 1))
-        return TSMM_ERR_UNSUPPORTED_SHAPE;  // before any device query
+    if (regime == 0) return TSMM_ERR_UNSUPPORTED_SHAPE;  // before any device query
     const int dev = current_device();
     if (dev < 0) return TSMM_ERR_CUDA;
     int sms = 0;
@@ -264,8 +267,7 @@ tsmm_status plan_layout(int64_t m, int64_t n, int64_t k, tsmm_dtype dtype, int f
                         size_t *ticket_bytes_out) {
     if (!valid_dtype(dtype) || m < 0 || n < 0 || k < 0) return TSMM_ERR_INVALID_ARG;
     const int regime = regime_of(k, n);
-    if (regime == 0 || (precision == TSMM_PREC_BF16X3 && regime != 1))
-        return TSMM_ERR_UNSUPPORTED_SHAPE;
+    if (regime == 0) return TSMM_ERR_UNSUPPORTED_SHAPE;
     std::memset(static_cast<void *>(p), 0, sizeof(*p));
     p->m = m;
     p->n = n;
@@ -277,7 +279,15 @@ tsmm_status plan_layout(int64_t m, int64_t n, int64_t k, tsmm_dtype dtype, int f
     p->num_sms = sms;
     const size_t es = dtype_size(dtype);
     size_t ticket_bytes = 0;
-    if (precision == TSMM_PREC_BF16X3) {
+    if (precision == TSMM_PREC_BF16X3 && regime == 2) {
+        // 128 x 128 output tiles, k (<= 128) in one or two 64-column chunks
+        p->kp = round_up(k, kX3KB);
+        p->bm = 128;
+        p->np = kX3RankNT;
+        p->splits = 1;
+        p->mtiles = (m + p->bm - 1) / p->bm;
+        p->ntiles = (n + kX3RankNT - 1) / kX3RankNT;
+    } else if (precision == TSMM_PREC_BF16X3) {
         // one 128-row slab per block, k in 64-column chunks, one block per SM
         p->np = x3_np(n);
         p->bm = 128;
@@ -429,6 +439,22 @@ tsmm_status tsmm_execute(tsmm_plan_t p, double alpha, const void *A_dev, int64_t
     }
     if (p->precision == TSMM_PREC_BF16X3) {
         if (!tma) return TSMM_ERR_MISALIGNED;  // this mode streams A with TMA only
+        if (p->regime == 2) {
+            RankArgs ra;
+            ra.m = m;
+            ra.n = n;
+            ra.k = k;
+            ra.lda = lda;
+            ra.ldc = ldc;
+            ra.kp = pb->kp;
+            ra.A = A_dev;
+            ra.Bp = pb->data;
+            ra.C = C_dev;
+            ra.alpha = alpha;
+            ra.beta = beta;
+            ra.num_sms = p->num_sms;
+            return cuda_status(launch_rankk_bf16x3(&p->tmap, ra, p->status, s));
+        }
         return cuda_status(launch_tall_bf16x3(p->np, &p->tmap, a, p->num_sms, s));
     }
     if (p->regime == 2) {

@@ -109,23 +109,29 @@ struct X3Cfg {
 
 }  // namespace
 
-// Pack B (k x n, column-major) for this kernel: per 64-row chunk c, a hi tile
-// and a lo tile, each NP rows (columns of B) x 64 k in the K-major layout
-// above; zero outside the k x n matrix.
+// Pack B (k x n, column-major) for the BF16x3 kernels: the columns are cut
+// into `ntiles` tiles of NP columns (one tile for regime (i)); per tile and per
+// 64-row chunk c of k, a hi tile then a lo tile, each NP rows (columns of B) x
+// 64 k in the K-major layout above; zero outside the k x n matrix.
 __global__ void pack_b_bf16x3_kernel(const float *__restrict__ B, int64_t k, int64_t n, int64_t ldb,
-                                     unsigned char *__restrict__ dst, int np, int64_t nchunks) {
-    const int64_t total = nchunks * np * kKB;
+                                     unsigned char *__restrict__ dst, int np, int64_t nchunks,
+                                     int64_t ntiles) {
+    const int64_t per_tile = nchunks * np * kKB;
+    const int64_t total = ntiles * per_tile;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
          e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t c = e / (np * kKB);
-        const int rem = (int)(e - c * np * kKB);
+        const int64_t t = e / per_tile;
+        const int64_t et = e - t * per_tile;
+        const int64_t c = et / (np * kKB);
+        const int rem = (int)(et - c * np * kKB);
         const int j = rem / kKB;
         const int kk = rem % kKB;
         const int64_t p = c * kKB + kk;
-        const float x = (p < k && j < n) ? B[p + j * ldb] : 0.f;
+        const int64_t col = t * np + j;
+        const float x = (p < k && col < n) ? B[p + col * ldb] : 0.f;
         const __nv_bfloat16 hi = __float2bfloat16_rn(x);
         const __nv_bfloat16 lo = __float2bfloat16_rn(x - __bfloat162float(hi));
-        unsigned char *chunk = dst + c * (int64_t)(2 * np * kKB * 2);
+        unsigned char *chunk = dst + (t * nchunks + c) * (int64_t)(2 * np * kKB * 2);
         *reinterpret_cast<__nv_bfloat16 *>(chunk + kmaj_off(j, kk)) = hi;
         *reinterpret_cast<__nv_bfloat16 *>(chunk + np * kKB * 2 + kmaj_off(j, kk)) = lo;
     }
@@ -437,14 +443,330 @@ cudaError_t launch_tall_bf16x3(int np, const CUtensorMap *tmap, const TallArgs &
 }
 
 cudaError_t launch_pack_b_bf16x3(int64_t k, int64_t n, const void *B, int64_t ldb, void *dst, int np,
-                                 int64_t nchunks, cudaStream_t s) {
-    const int64_t total = nchunks * np * kKB;
+                                 int64_t nchunks, int64_t ntiles, cudaStream_t s) {
+    const int64_t total = ntiles * nchunks * np * kKB;
     if (total == 0) return cudaSuccess;
     int64_t blocks = (total + 255) / 256;
     if (blocks > 152 * 64) blocks = 152 * 64;
     pack_b_bf16x3_kernel<<<(unsigned)blocks, 256, 0, s>>>(static_cast<const float *>(B), k, n, ldb,
-                                                          static_cast<unsigned char *>(dst), np, nchunks);
+                                                          static_cast<unsigned char *>(dst), np, nchunks,
+                                                          ntiles);
     return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Regime (ii) (k <= 128, m and n large) in the BF16x3 mode.  The cost of this
+// shape is the m x n output stream (C0 in, C out); the tensor cores make the
+// k-term products nearly free.  Persistent blocks walk work items = (m-tile of
+// 128 rows, chunk of kRNCH n-tiles of 128 columns).  Per item the producer
+// brings the FP32 A tile (128 x kp) once and the converters split it in place
+// into hi|lo BF16; then the pre-split B tiles of the chunk stream through a
+// double buffer, one thread issues the 3 x kp/16 MMAs of each tile (M = N =
+// 128) into one of two TMEM accumulators, and eight epilogue warps (two per
+// TMEM lane quarter, 64 columns each) read an accumulator, release it, and
+// stream alpha*acc + beta*C0 to C with coalesced loads and stores.
+namespace {
+
+constexpr int kRNCH = 8;  // n-tiles per work item
+
+template <int KC>  // 64-column k chunks: 1 (k <= 64) or 2 (k <= 128)
+struct RX3Cfg {
+    static constexpr int NT = kX3RankNT;                  // 128 columns per tile
+    static constexpr int A_BYTES = KC * kBM * kKB * 4;    // FP32 in, then hi|lo per chunk, in place
+    static constexpr int B_TILE = KC * 2 * NT * kKB * 2;  // hi|lo per chunk
+    static constexpr int OFF_B = A_BYTES;
+    static constexpr int OFF_BAR = OFF_B + 2 * B_TILE;
+    static constexpr int NBAR = 3 + 2 + 2 + 2 + 2 + 1;
+    static constexpr int SMEM = OFF_BAR + NBAR * 8 + 32;
+    static constexpr int TMEM_COLS = 2 * NT;
+    static constexpr int THREADS = 14 * 32;
+};
+
+}  // namespace
+
+template <int KC>
+__global__ void __launch_bounds__(448, 1)
+    rankk_bf16x3_kernel(const __grid_constant__ CUtensorMap tmA, const RankArgs a, unsigned *status) {
+    using Cfg = RX3Cfg<KC>;
+    constexpr int NT = Cfg::NT;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + Cfg::OFF_BAR);
+    uint64_t *a_full = bar;        // FP32 A tile landed
+    uint64_t *a_conv = bar + 1;    // hi|lo written (4 converter warps)
+    uint64_t *a_empty = bar + 2;   // the item's MMAs are done with A
+    uint64_t *b_full = bar + 3;    // [2]
+    uint64_t *b_empty = bar + 5;   // [2]
+    uint64_t *tfull = bar + 7;     // [2]
+    uint64_t *tempty = bar + 9;    // [2] (8 epilogue warps)
+    uint64_t *done = bar + 11;
+    unsigned *tslot = reinterpret_cast<unsigned *>(bar + Cfg::NBAR);
+    unsigned *conv_abort = tslot + 1;
+    unsigned *ep_abort = tslot + 2;
+
+    const int warp = threadIdx.x / 32;
+    const int lane = threadIdx.x % 32;
+    const int64_t mtiles = (a.m + kBM - 1) / kBM;
+    const int64_t ntiles = (a.n + NT - 1) / NT;
+    const int64_t nch = (ntiles + kRNCH - 1) / kRNCH;
+    const int64_t total = mtiles * nch;
+
+    if (threadIdx.x == 0) {
+        prefetch_tmap(&tmA);
+        mbar_init(a_full, 1);
+        mbar_init(a_conv, 4);
+        mbar_init(a_empty, 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&b_full[b], 1);
+            mbar_init(&b_empty[b], 1);
+            mbar_init(&tfull[b], 1);
+            mbar_init(&tempty[b], 8);
+        }
+        mbar_init(done, 1);
+        *conv_abort = 0u;
+        *ep_abort = 0u;
+        fence_mbar_init();
+    }
+    if (warp == 5) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_addr(tslot)),
+                     "r"((uint32_t)Cfg::TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+
+    if (warp == 4) {
+        // ------------------------------------------------ producer
+        if (lane == 0) {
+            const uint64_t pol_a = policy_evict_last();  // A tiles are re-read by other n-chunks
+            const uint64_t pol_b = policy_evict_last();
+            const unsigned char *Bp = static_cast<const unsigned char *>(a.Bp);
+            int64_t g = 0;
+            int j = 0;
+            bool ok = true;
+            for (int64_t item = blockIdx.x; item < total && ok; item += gridDim.x, ++j) {
+                const int64_t mt = item / nch;
+                const int64_t t0 = (item % nch) * kRNCH;
+                const int64_t t1 = (t0 + kRNCH < ntiles) ? t0 + kRNCH : ntiles;
+                if (j >= 1 && !mbar_wait_bounded(a_empty, (uint32_t)((j - 1) & 1))) {
+                    ok = false;
+                    break;
+                }
+                mbar_arrive_expect_tx(a_full, Cfg::A_BYTES);
+                for (int box = 0; box < 2 * KC; ++box)
+                    tma_load_2d(smem + box * (kBM * 32 * 4), &tmA, (int32_t)(mt * kBM), (int32_t)(box * 32),
+                                a_full, pol_a);
+                for (int64_t t = t0; t < t1; ++t, ++g) {
+                    const int sb = (int)(g & 1);
+                    if (g >= 2 && !mbar_wait_bounded(&b_empty[sb], (uint32_t)((g >> 1) & 1) ^ 1)) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_arrive_expect_tx(&b_full[sb], Cfg::B_TILE);
+                    bulk_load(smem + Cfg::OFF_B + sb * Cfg::B_TILE, Bp + t * Cfg::B_TILE, Cfg::B_TILE,
+                              &b_full[sb], pol_b);
+                }
+            }
+            if (!ok) atomicOr(status, kDevErrTimeout);
+        }
+        return;
+    }
+
+    if (warp == 5) {
+        // ------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            constexpr uint32_t idesc = umma_idesc(kBM, NT);
+            int64_t g = 0;
+            int j = 0;
+            bool ok = true;
+            for (int64_t item = blockIdx.x; item < total && ok; item += gridDim.x, ++j) {
+                const int64_t t0 = (item % nch) * kRNCH;
+                const int64_t t1 = (t0 + kRNCH < ntiles) ? t0 + kRNCH : ntiles;
+                if (!mbar_wait_bounded(a_conv, (uint32_t)(j & 1))) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                for (int64_t t = t0; t < t1; ++t, ++g) {
+                    const int sb = (int)(g & 1);
+                    if (!mbar_wait_bounded(&b_full[sb], (uint32_t)((g >> 1) & 1)) ||
+                        (g >= 2 && !mbar_wait_bounded(&tempty[sb], (uint32_t)((g >> 1) & 1) ^ 1))) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t tacc = tmem + (uint32_t)(sb * NT);
+#pragma unroll
+                    for (int c = 0; c < KC; ++c) {
+                        const uint32_t ahi = smem_addr(smem + c * (kBM * kKB * 4));
+                        const uint32_t alo = ahi + kBM * kKB * 2;
+                        const uint32_t bhi = smem_addr(smem + Cfg::OFF_B + sb * Cfg::B_TILE + c * (2 * NT * kKB * 2));
+                        const uint32_t blo = bhi + NT * kKB * 2;
+#pragma unroll
+                        for (int ks = 0; ks < kKB / 16; ++ks) {
+                            const uint32_t off = ks * 2 * kLBO;
+                            umma_bf16(tacc, umma_desc(ahi + off), umma_desc(bhi + off), idesc,
+                                      (c | ks) != 0 ? 1u : 0u);
+                            umma_bf16(tacc, umma_desc(ahi + off), umma_desc(blo + off), idesc, 1u);
+                            umma_bf16(tacc, umma_desc(alo + off), umma_desc(bhi + off), idesc, 1u);
+                        }
+                    }
+                    umma_commit(&b_empty[sb]);
+                    umma_commit(&tfull[sb]);
+                }
+                if (ok) umma_commit(a_empty);
+            }
+            umma_commit(done);
+            if (!ok) atomicOr(status, kDevErrTimeout);
+            mbar_wait_bounded(done, 0);
+        }
+        __syncwarp();
+        tc_fence_before();
+        named_barrier(2, 288);  // warps 5..13
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"((uint32_t)Cfg::TMEM_COLS));
+        return;
+    }
+
+    if (warp < 4) {
+        // ------------------------------------------------ converters: A tile in place
+        const int r = threadIdx.x;
+        int j = 0;
+        for (int64_t item = blockIdx.x; item < total; item += gridDim.x, ++j) {
+            const bool got = mbar_wait_bounded(a_full, (uint32_t)(j & 1));
+            if (!got && lane == 0) atomicOr(conv_abort, 1u);
+            named_barrier(1, 128);
+            const bool stop = *conv_abort != 0u;
+            named_barrier(1, 128);
+            if (stop) {
+                if (r == 0) atomicOr(status, kDevErrTimeout);
+                break;
+            }
+#pragma unroll
+            for (int c = 0; c < KC; ++c) {
+                unsigned char *stage = smem + c * (kBM * kKB * 4);
+                const float *src = reinterpret_cast<const float *>(stage);  // [64][128] FP32
+                float x[kKB];
+#pragma unroll
+                for (int q = 0; q < kKB; ++q) x[q] = src[q * kBM + r];
+                named_barrier(1, 128);  // the whole chunk is read before it is overwritten
+                unsigned char *hi = stage;
+                unsigned char *lo = stage + kBM * kKB * 2;
+#pragma unroll
+                for (int kg = 0; kg < kKB / 8; ++kg) {
+                    uint32_t h[4], l[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const float x0 = x[kg * 8 + 2 * q];
+                        const float x1 = x[kg * 8 + 2 * q + 1];
+                        const __nv_bfloat162 hv = __floats2bfloat162_rn(x0, x1);
+                        const float2 hf = __bfloat1622float2(hv);
+                        const __nv_bfloat162 lv = __floats2bfloat162_rn(x0 - hf.x, x1 - hf.y);
+                        h[q] = *reinterpret_cast<const uint32_t *>(&hv);
+                        l[q] = *reinterpret_cast<const uint32_t *>(&lv);
+                    }
+                    const int off = kmaj_off(r, kg * 8);
+                    *reinterpret_cast<uint4 *>(hi + off) = make_uint4(h[0], h[1], h[2], h[3]);
+                    *reinterpret_cast<uint4 *>(lo + off) = make_uint4(l[0], l[1], l[2], l[3]);
+                }
+            }
+            fence_proxy_async_smem();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(a_conv);
+        }
+        return;
+    }
+
+    // ---------------------------------------------------- epilogue (warps 6-13)
+    const int quarter = warp % 4;
+    const int half = (warp - 6) / 4;
+    const float alpha = static_cast<float>(a.alpha);
+    const float beta = static_cast<float>(a.beta);
+    float *C = static_cast<float *>(a.C);
+    int64_t g = 0;
+    bool stop = false;
+    for (int64_t item = blockIdx.x; item < total && !stop; item += gridDim.x) {
+        const int64_t mt = item / nch;
+        const int64_t t0 = (item % nch) * kRNCH;
+        const int64_t t1 = (t0 + kRNCH < ntiles) ? t0 + kRNCH : ntiles;
+        const int64_t i = mt * kBM + quarter * 32 + lane;
+        for (int64_t t = t0; t < t1; ++t, ++g) {
+            const int tb = (int)(g & 1);
+            const bool got = mbar_wait_bounded(&tfull[tb], (uint32_t)((g >> 1) & 1));
+            if (!got && lane == 0) atomicOr(ep_abort, 1u);
+            named_barrier(3, 256);
+            stop = *ep_abort != 0u;
+            named_barrier(3, 256);
+            if (stop) {
+                if (warp == 6 && lane == 0) atomicOr(status, kDevErrTimeout);
+                break;
+            }
+            tc_fence_after();
+            const int64_t j0 = t * NT + half * 64;
+            float *crow = C + i;
+            // all 64 C0 loads of this thread's half row are issued before any
+            // store: 64 KB of reads in flight per SM keep HBM busy
+            float c0v[64];
+            if (beta != 0.f && i < a.m) {
+#pragma unroll
+                for (int jj = 0; jj < 64; ++jj)
+                    c0v[jj] = (j0 + jj < a.n) ? crow[(j0 + jj) * a.ldc] : 0.f;
+            }
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                float acc[16];
+                tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(tb * NT + half * 64 + b * 16),
+                          acc);
+                if (b == 3) {
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&tempty[tb]);  // the accumulator may be refilled
+                }
+                if (i < a.m) {
+#pragma unroll
+                    for (int jj = 0; jj < 16; ++jj) {
+                        const int64_t jc = j0 + b * 16 + jj;
+                        if (jc < a.n) {
+                            float o = (alpha == 1.f) ? acc[jj] : alpha * acc[jj];
+                            if (beta != 0.f) o = fmaf(beta, c0v[b * 16 + jj], o);
+                            crow[jc * a.ldc] = o;
+                        }
+                    }
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    named_barrier(2, 288);  // with warp 5, before it frees TMEM
+}
+
+template <int KC>
+static cudaError_t launch_rx3_t(const CUtensorMap *tmA, const RankArgs &a, unsigned *status,
+                                cudaStream_t s) {
+    using Cfg = RX3Cfg<KC>;
+    static bool attr_done = false;
+    if (!attr_done) {
+        cudaError_t e = cudaFuncSetAttribute(rankk_bf16x3_kernel<KC>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
+        if (e != cudaSuccess) return e;
+        attr_done = true;
+    }
+    const int64_t mtiles = (a.m + kBM - 1) / kBM;
+    const int64_t ntiles = (a.n + Cfg::NT - 1) / Cfg::NT;
+    const int64_t items = mtiles * ((ntiles + kRNCH - 1) / kRNCH);
+    const int64_t slots = a.num_sms > 0 ? a.num_sms : 1;
+    const unsigned grid = (unsigned)(items < slots ? items : slots);
+    if (grid == 0) return cudaSuccess;
+    rankk_bf16x3_kernel<KC><<<grid, Cfg::THREADS, Cfg::SMEM, s>>>(*tmA, a, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rankk_bf16x3(const CUtensorMap *tmA, const RankArgs &a, unsigned *status,
+                                cudaStream_t s) {
+    return a.kp <= kKB ? launch_rx3_t<1>(tmA, a, status, s) : launch_rx3_t<2>(tmA, a, status, s);
 }
 
 }  // namespace tsmm

@@ -146,7 +146,11 @@ inline int x3_np(int64_t n) {
 cudaError_t launch_tall_bf16x3(int np, const CUtensorMap *tmap, const TallArgs &a, int num_sms,
                                cudaStream_t s);
 cudaError_t launch_pack_b_bf16x3(int64_t k, int64_t n, const void *B, int64_t ldb, void *dst, int np,
-                                 int64_t nchunks, cudaStream_t s);
+                                 int64_t nchunks, int64_t ntiles, cudaStream_t s);
+// Regime (ii) in the BF16x3 mode: tile width of its packed B, and the kernel.
+constexpr int kX3RankNT = 128;
+cudaError_t launch_rankk_bf16x3(const CUtensorMap *tmA, const RankArgs &a, unsigned *status,
+                                cudaStream_t s);
 
 // Process-wide plan cache (tsmm_tune.cu): tuned split counts keyed by
 // (dtype, m, n, k, SM count).  Lookup returns 0 when absent.

@@ -99,3 +99,7 @@ def test_plan_cache_file_roundtrip(tmp_path):
     assert tsmm.tsmm_plan_cache_size() == 2
     tsmm.tsmm_plan_cache_clear()
     assert tsmm.tsmm_plan_cache_size() == 0
+
+
+def test_last_cuda_error_string():
+    assert isinstance(tsmm.lib.tsmm_last_cuda_error().decode(), str)

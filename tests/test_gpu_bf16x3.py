@@ -90,9 +90,6 @@ def test_bf16x3_errors():
     with pytest.raises(tsmm.TsmmError) as e:  # FP64 has no BF16x3 mode
         tsmm.plan(50, 16, 100, torch.float64, precision=X3)
     assert e.value.status == 1
-    with pytest.raises(tsmm.TsmmError) as e:  # regime (ii) not in this mode
-        tsmm.plan(500, 200, 64, torch.float32, precision=X3)
-    assert e.value.status == 2
     pb = tsmm.pack_b(B, precision=X3)
     A_odd = to_device(ti.matrix_np(50, 100, 1, "uniform", np.float32), offset=1)
     with pytest.raises(tsmm.TsmmError) as e:  # TMA-only mode: unaligned A
@@ -149,5 +146,57 @@ def test_bf16x3_full_size_sampled():
     Cref, _ = oracle.tsmm(1.0, A_r, B, 0.0, None)
     C = dC[torch.as_tensor(rows, device="cuda")].cpu().numpy()
     E3 = x3_bound(A_r, B, None, 1.0, 0.0)
+    err = np.abs(C.astype(np.float64) - Cref)
+    assert np.all(err <= E3), f"max err/bound {np.max(err / E3):.3g}"
+
+
+@pytest.mark.parametrize("m,n,k,beta", [(1000, 300, 64, 1.0), (2050, 1000, 128, 1.0), (515, 129, 33, 0.0),
+                                        (4096, 2048, 100, -0.5), (300, 5000, 16, 1.0)])
+def test_bf16x3_rankk_integer_bit_exact(m, n, k, beta):
+    """Regime (ii) in the tensor-core mode: integer inputs are exact."""
+    A = ti.matrix_np(m, k, 61, "integer", np.float32)
+    B = ti.matrix_np(k, n, 62, "integer", np.float32)
+    C0 = ti.matrix_np(m, n, 63, "integer", np.float32)
+    C, pl = run_x3(A, B, C0 if beta else None, 1.5, beta)
+    assert pl.info()["regime"] == 2
+    Cref, _ = oracle.tsmm(1.5, A, B, beta, C0 if beta else None)
+    np.testing.assert_array_equal(C, oracle.round_to(Cref, np.float32))
+
+
+@pytest.mark.parametrize("m,n,k", [(2000, 1500, 128), (1000, 700, 64)])
+def test_bf16x3_rankk_uniform_within_mode_bound(m, n, k):
+    A = ti.matrix_np(m, k, 71, "uniform", np.float32)
+    B = ti.matrix_np(k, n, 72, "uniform", np.float32)
+    C0 = ti.matrix_np(m, n, 73, "uniform", np.float32)
+    C, _ = run_x3(A, B, C0, 1.0, 1.0)
+    Cref, _ = oracle.tsmm(1.0, A, B, 1.0, C0)
+    E3 = x3_bound(A, B, C0, 1.0, 1.0)
+    err = np.abs(C.astype(np.float64) - Cref)
+    assert np.all(err <= E3), f"max err/bound {np.max(err / E3):.3g}"
+
+
+def test_bf16x3_rankk_full_size_sampled():
+    """m = n = 16384, k = 128 (the precision workload's rank-k shape)."""
+    m = n = 16384
+    k = 128
+    dA = torch.empty((k, m), dtype=torch.float32, device="cuda")
+    ti.fill_torch(dA, ti.SEED_A, "uniform")
+    dA = dA.t()
+    dB = torch.empty((n, k), dtype=torch.float32, device="cuda")
+    ti.fill_torch(dB, ti.SEED_B, "uniform")
+    dB = dB.t()
+    dC = torch.empty((n, m), dtype=torch.float32, device="cuda")
+    ti.fill_torch(dC, ti.SEED_C0, "uniform")
+    dC = dC.t()
+    pl = tsmm.plan(m, n, k, torch.float32, precision=X3)
+    tsmm.execute(pl, 1.0, dA, tsmm.pack_b(dB, precision=X3), 1.0, dC)
+    pl.check()
+    rows = np.sort(np.random.default_rng(9).choice(m, 16, replace=False))
+    A_r = np.asfortranarray(ti.rows_np(rows, m, k, ti.SEED_A, "uniform", np.float32))
+    B = ti.matrix_np(k, n, ti.SEED_B, "uniform", np.float32)
+    C0_r = np.asfortranarray(ti.rows_np(rows, m, n, ti.SEED_C0, "uniform", np.float32))
+    Cref, _ = oracle.tsmm(1.0, A_r, B, 1.0, C0_r)
+    C = dC[torch.as_tensor(rows, device="cuda")].cpu().numpy()
+    E3 = x3_bound(A_r, B, C0_r, 1.0, 1.0)
     err = np.abs(C.astype(np.float64) - Cref)
     assert np.all(err <= E3), f"max err/bound {np.max(err / E3):.3g}"

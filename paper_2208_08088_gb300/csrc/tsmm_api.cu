@@ -52,6 +52,36 @@ int current_device() {
     return dev;
 }
 
+// C may be read by TMA: 16-byte aligned base and column stride, sizes in range.
+bool c_tma_ok(const void *C_dev, int64_t ldc, int64_t n, size_t es) {
+    return aligned(C_dev, 16) && ((ldc * (int64_t)es) % 16 == 0) && n < INT_MAX &&
+           (ldc * (int64_t)es) < (1LL << 40) && encoder() != nullptr;
+}
+
+// (Re)encode the plan's cached tensor map of C (box 128-or-bm rows x `cols`)
+// when C's address or stride changed since the last execute.
+tsmm_status encode_tmapc(tsmm_plan_t p, void *C_dev, int64_t m, int64_t n, int64_t ldc, size_t es,
+                         int cols) {
+    if (p->tmapc_ptr == C_dev && p->tmapc_ldc == ldc) return TSMM_OK;
+    const cuuint64_t gdim[2] = {(cuuint64_t)m, (cuuint64_t)n};
+    const cuuint64_t gstride[1] = {(cuuint64_t)(ldc * (int64_t)es)};
+    const cuuint32_t box[2] = {(cuuint32_t)p->bm, (cuuint32_t)cols};
+    const cuuint32_t estr[2] = {1, 1};
+    CUresult r = encoder()(&p->tmapc,
+                           p->dtype == TSMM_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                                : CU_TENSOR_MAP_DATA_TYPE_FLOAT64,
+                           2, C_dev, gdim, gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                           CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        p->tmapc_ptr = nullptr;
+        return TSMM_ERR_CUDA;
+    }
+    p->tmapc_ptr = C_dev;
+    p->tmapc_ldc = ldc;
+    return TSMM_OK;
+}
+
 }  // namespace
 
 namespace tsmm {
@@ -453,7 +483,13 @@ tsmm_status tsmm_execute(tsmm_plan_t p, double alpha, const void *A_dev, int64_t
             ra.alpha = alpha;
             ra.beta = beta;
             ra.num_sms = p->num_sms;
-            return cuda_status(launch_rankk_bf16x3(&p->tmap, ra, p->status, s));
+            // C0 loads and C stores go through TMA when C allows it (any beta)
+            const bool tmc = c_tma_ok(C_dev, ldc, n, es);
+            if (tmc) {
+                const tsmm_status st = encode_tmapc(p, C_dev, m, n, ldc, es, kX3RankSub);
+                if (st != TSMM_OK) return st;
+            }
+            return cuda_status(launch_rankk_bf16x3(&p->tmap, tmc ? &p->tmapc : nullptr, ra, p->status, s));
         }
         return cuda_status(launch_tall_bf16x3(p->np, &p->tmap, a, p->num_sms, s));
     }
@@ -472,27 +508,10 @@ tsmm_status tsmm_execute(tsmm_plan_t p, double alpha, const void *A_dev, int64_t
         ra.beta = beta;
         ra.num_sms = p->num_sms;
         // C0 tile prefetch by TMA: needs the same 16-byte rules for C
-        const bool tmc = tma && beta != 0.0 && aligned(C_dev, 16) &&
-                         ((ldc * (int64_t)es) % 16 == 0) && n < INT_MAX &&
-                         (ldc * (int64_t)es) < (1LL << 40);
-        if (tmc && (p->tmapc_ptr != C_dev || p->tmapc_ldc != ldc)) {
-            const cuuint64_t gdim[2] = {(cuuint64_t)m, (cuuint64_t)n};
-            const cuuint64_t gstride[1] = {(cuuint64_t)(ldc * (int64_t)es)};
-            const cuuint32_t box[2] = {(cuuint32_t)p->bm, (cuuint32_t)kRankNT};
-            const cuuint32_t estr[2] = {1, 1};
-            CUresult r = encoder()(&p->tmapc,
-                                   p->dtype == TSMM_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
-                                                        : CU_TENSOR_MAP_DATA_TYPE_FLOAT64,
-                                   2, C_dev, gdim, gstride, box, estr,
-                                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-            if (r != CUDA_SUCCESS) {
-                p->tmapc_ptr = nullptr;
-                return TSMM_ERR_CUDA;
-            }
-            p->tmapc_ptr = C_dev;
-            p->tmapc_ldc = ldc;
+        const bool tmc = tma && beta != 0.0 && c_tma_ok(C_dev, ldc, n, es);
+        if (tmc) {
+            const tsmm_status st = encode_tmapc(p, C_dev, m, n, ldc, es, kRankNT);
+            if (st != TSMM_OK) return st;
         }
         return cuda_status(launch_rankk(p->dtype, tma ? &p->tmap : nullptr, tmc ? &p->tmapc : nullptr,
                                         ra, p->status, s));

@@ -29,6 +29,8 @@
 // 1 KB apart along rows (SBO = 1024 B).
 #include <cuda_bf16.h>
 
+#include <cstring>
+
 #include "tsmm_device.cuh"
 #include "tsmm_internal.h"
 
@@ -458,72 +460,168 @@ cudaError_t launch_pack_b_bf16x3(int64_t k, int64_t n, const void *B, int64_t ld
 // Regime (ii) (k <= 128, m and n large) in the BF16x3 mode.  The cost of this
 // shape is the m x n output stream (C0 in, C out); the tensor cores make the
 // k-term products nearly free.  Persistent blocks walk work items = (m-tile of
-// 128 rows, chunk of kRNCH n-tiles of 128 columns).  Per item the producer
-// brings the FP32 A tile (128 x kp) once and the converters split it in place
-// into hi|lo BF16; then the pre-split B tiles of the chunk stream through a
-// double buffer, one thread issues the 3 x kp/16 MMAs of each tile (M = N =
-// 128) into one of two TMEM accumulators, and eight epilogue warps (two per
-// TMEM lane quarter, 64 columns each) read an accumulator, release it, and
-// stream alpha*acc + beta*C0 to C with coalesced loads and stores.
+// 128 rows, chunk of `rnch` n-tiles of 128 columns), with 16 warps:
+//   warp 4      producer: the FP32 A tile (128 x kp) once per item, then the
+//               pre-split B chunks (hi|lo, 64 k x 128 columns, 32 KB) of the
+//               item's tiles through a ring of NB chunk buffers;
+//   warps 0-3   converters: split the A tile in place into hi|lo BF16;
+//   warp 5      allocates TMEM; lane 0 issues the 3 x kp/16 MMAs of a tile
+//               (M = N = 128) into one of two TMEM accumulators;
+//   warps 6-13  epilogue: two per TMEM lane quarter, each owning 64 columns
+//               (two 32-column sub-tiles) of a tile: one tcgen05.ld of its 32
+//               rows x 64 accumulator columns, then per sub-tile
+//               alpha*acc + beta*C0;
+//   warp 14     C0 loader (beta != 0): 128 x 32 sub-tiles of C0 into a ring
+//               of CS shared-memory slots;
+//   warp 15     storer: TMA stores of finished sub-tiles from their slots.
+// When C meets the TMA rules (16-byte aligned base and column stride) each
+// sub-tile lives in one slot from C0 load to C store: the epilogue overwrites
+// C0 with the result in place, the storer writes it out by TMA and frees the
+// slot, so every global access of the output stream is a bulk copy.  Otherwise
+// C0 arrives by 4-byte cp.async and the epilogue stores C directly (one
+// 128-byte line per warp store).
 namespace {
 
-constexpr int kRNCH = 8;  // n-tiles per work item
+constexpr int kRNCHMax = 16;       // n-tiles per work item, at most
+constexpr int kRSUB = kX3RankSub;  // columns per sub-tile (TMA box 128 x 32 FP32 = 16 KB)
+constexpr int kRSUBS = kX3RankNT / kRSUB;
 
 template <int KC>  // 64-column k chunks: 1 (k <= 64) or 2 (k <= 128)
 struct RX3Cfg {
-    static constexpr int NT = kX3RankNT;                  // 128 columns per tile
-    static constexpr int A_BYTES = KC * kBM * kKB * 4;    // FP32 in, then hi|lo per chunk, in place
-    static constexpr int B_TILE = KC * 2 * NT * kKB * 2;  // hi|lo per chunk
-    static constexpr int OFF_B = A_BYTES;
-    static constexpr int OFF_BAR = OFF_B + 2 * B_TILE;
-    static constexpr int NBAR = 3 + 2 + 2 + 2 + 2 + 1;
-    static constexpr int SMEM = OFF_BAR + NBAR * 8 + 32;
+    static constexpr int NT = kX3RankNT;               // 128 columns per tile
+    static constexpr int A_BYTES = KC * kBM * kKB * 4; // FP32 in, then hi|lo per chunk, in place
+    static constexpr int B_CHUNK = 2 * NT * kKB * 2;   // hi|lo of one 64-k chunk of one tile
+    static constexpr int B_TILE = KC * B_CHUNK;
+    static constexpr int NB = KC == 1 ? 2 : 3;         // B chunk buffers
+    static constexpr int CS = KC == 1 ? 8 : 4;         // C slots
+    static constexpr int SLOT = kBM * kRSUB * 4;
+    static constexpr int OFF_BAR = 0;                  // barriers first
+    static constexpr int OFF_A = 1024;
+    static constexpr int OFF_B = OFF_A + A_BYTES;
+    static constexpr int OFF_C = OFF_B + NB * B_CHUNK;
+    static constexpr int NBAR = 3 + 2 * NB + 2 + 2 + 1 + 3 * CS;
+    static constexpr int SMEM = OFF_C + CS * SLOT;
+    static constexpr int SMEM_NO_SLOTS = OFF_C;        // beta == 0 and C not TMA-able
     static constexpr int TMEM_COLS = 2 * NT;
-    static constexpr int THREADS = 14 * 32;
+    static constexpr int THREADS = 16 * 32;
+    static_assert(NBAR * 8 + 32 <= OFF_A, "barrier area");
+    static_assert(SMEM <= 227 * 1024, "shared memory");
 };
+
+__device__ __forceinline__ void cp_async4(void *smem_dst, const void *gsrc, uint32_t src_bytes) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(smem_addr(smem_dst)),
+                 "l"(reinterpret_cast<uint64_t>(gsrc)), "r"(src_bytes)
+                 : "memory");
+}
+
+// Arrive on `bar` once every earlier cp.async of this thread has landed (the
+// barrier's expected count includes this arrival).
+__device__ __forceinline__ void cp_async_mbar_arrive(uint64_t *bar) {
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+// 2-D tiled tensor copy shared -> global (out-of-range parts of the box are
+// not written); tracked by this thread's bulk async-groups.
+__device__ __forceinline__ void tma_store_2d(const void *tmap, const void *smem_src, int32_t x, int32_t y) {
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+                     reinterpret_cast<uint64_t>(tmap)),
+                 "r"(x), "r"(y), "r"(smem_addr(smem_src))
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// every committed store has finished reading shared memory
+__device__ __forceinline__ void bulk_wait_read_all() {
+    asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+// every committed store is complete
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
+// 64 consecutive FP32 accumulator columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld64(uint32_t taddr, float *out) {
+    uint32_t r[64];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x64.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,"
+        "%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,"
+        "%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%64];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+          "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+          "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+          "=r"(r[29]), "=r"(r[30]), "=r"(r[31]), "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]),
+          "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]), "=r"(r[40]), "=r"(r[41]), "=r"(r[42]),
+          "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]), "=r"(r[48]), "=r"(r[49]),
+          "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]), "=r"(r[56]),
+          "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
+        : "r"(taddr)
+        : "memory");
+#pragma unroll
+    for (int j = 0; j < 64; ++j) out[j] = __uint_as_float(r[j]);
+}
+
+// Warp-uniform bounded wait: every lane polls, and the warp proceeds only if
+// all lanes saw the phase complete.
+__device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity) {
+    return __all_sync(0xffffffffu, mbar_wait_bounded(bar, parity));
+}
 
 }  // namespace
 
 template <int KC>
-__global__ void __launch_bounds__(448, 1)
-    rankk_bf16x3_kernel(const __grid_constant__ CUtensorMap tmA, const RankArgs a, unsigned *status) {
+__global__ void __launch_bounds__(512, 1)
+    rankk_bf16x3_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmC,
+                        const RankArgs a, unsigned *status, int c_tma, int rnch) {
     using Cfg = RX3Cfg<KC>;
     constexpr int NT = Cfg::NT;
+    constexpr int NB = Cfg::NB;
+    constexpr int CS = Cfg::CS;
     extern __shared__ __align__(1024) unsigned char smem[];
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem + Cfg::OFF_BAR);
-    uint64_t *a_full = bar;        // FP32 A tile landed
-    uint64_t *a_conv = bar + 1;    // hi|lo written (4 converter warps)
-    uint64_t *a_empty = bar + 2;   // the item's MMAs are done with A
-    uint64_t *b_full = bar + 3;    // [2]
-    uint64_t *b_empty = bar + 5;   // [2]
-    uint64_t *tfull = bar + 7;     // [2]
-    uint64_t *tempty = bar + 9;    // [2] (8 epilogue warps)
-    uint64_t *done = bar + 11;
+    uint64_t *a_full = bar;            // FP32 A tile landed
+    uint64_t *a_conv = bar + 1;        // hi|lo written (4 converter warps)
+    uint64_t *a_empty = bar + 2;       // the item's MMAs are done with A
+    uint64_t *b_full = bar + 3;        // [NB]
+    uint64_t *b_empty = b_full + NB;   // [NB]
+    uint64_t *tfull = b_empty + NB;    // [2]
+    uint64_t *tempty = tfull + 2;      // [2] (8 epilogue warps)
+    uint64_t *done = tempty + 2;
+    uint64_t *c_full = done + 1;       // [CS] C0 landed in the slot
+    uint64_t *c_store = c_full + CS;   // [CS] results written to the slot (4 warps)
+    uint64_t *c_empty = c_store + CS;  // [CS] slot free again
     unsigned *tslot = reinterpret_cast<unsigned *>(bar + Cfg::NBAR);
     unsigned *conv_abort = tslot + 1;
-    unsigned *ep_abort = tslot + 2;
+    float *cslots = reinterpret_cast<float *>(smem + Cfg::OFF_C);
 
     const int warp = threadIdx.x / 32;
     const int lane = threadIdx.x % 32;
     const int64_t mtiles = (a.m + kBM - 1) / kBM;
     const int64_t ntiles = (a.n + NT - 1) / NT;
-    const int64_t nch = (ntiles + kRNCH - 1) / kRNCH;
+    const int64_t nch = (ntiles + rnch - 1) / rnch;
     const int64_t total = mtiles * nch;
+    const bool use_c0 = a.beta != 0.0;
 
     if (threadIdx.x == 0) {
         prefetch_tmap(&tmA);
+        if (c_tma) prefetch_tmap(&tmC);
         mbar_init(a_full, 1);
         mbar_init(a_conv, 4);
         mbar_init(a_empty, 1);
-        for (int b = 0; b < 2; ++b) {
+        for (int b = 0; b < NB; ++b) {
             mbar_init(&b_full[b], 1);
             mbar_init(&b_empty[b], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
             mbar_init(&tfull[b], 1);
             mbar_init(&tempty[b], 8);
         }
         mbar_init(done, 1);
+        for (int s = 0; s < CS; ++s) {
+            mbar_init(&c_full[s], c_tma ? 1 : 32);
+            mbar_init(&c_store[s], 4);
+            mbar_init(&c_empty[s], c_tma ? 1 : 4);
+        }
         *conv_abort = 0u;
-        *ep_abort = 0u;
         fence_mbar_init();
     }
     if (warp == 5) {
@@ -538,39 +636,121 @@ __global__ void __launch_bounds__(448, 1)
     const uint32_t tmem = *tslot;
 
     if (warp == 4) {
-        // ------------------------------------------------ producer
+        // ------------------------------------------------ producer: A and B
         if (lane == 0) {
             const uint64_t pol_a = policy_evict_last();  // A tiles are re-read by other n-chunks
             const uint64_t pol_b = policy_evict_last();
             const unsigned char *Bp = static_cast<const unsigned char *>(a.Bp);
-            int64_t g = 0;
+            int64_t gq = 0;  // B chunks issued
             int j = 0;
             bool ok = true;
             for (int64_t item = blockIdx.x; item < total && ok; item += gridDim.x, ++j) {
                 const int64_t mt = item / nch;
-                const int64_t t0 = (item % nch) * kRNCH;
-                const int64_t t1 = (t0 + kRNCH < ntiles) ? t0 + kRNCH : ntiles;
+                const int64_t t0 = (item % nch) * rnch;
+                const int64_t t1 = (t0 + rnch < ntiles) ? t0 + rnch : ntiles;
                 if (j >= 1 && !mbar_wait_bounded(a_empty, (uint32_t)((j - 1) & 1))) {
                     ok = false;
                     break;
                 }
                 mbar_arrive_expect_tx(a_full, Cfg::A_BYTES);
                 for (int box = 0; box < 2 * KC; ++box)
-                    tma_load_2d(smem + box * (kBM * 32 * 4), &tmA, (int32_t)(mt * kBM), (int32_t)(box * 32),
-                                a_full, pol_a);
-                for (int64_t t = t0; t < t1; ++t, ++g) {
-                    const int sb = (int)(g & 1);
-                    if (g >= 2 && !mbar_wait_bounded(&b_empty[sb], (uint32_t)((g >> 1) & 1) ^ 1)) {
-                        ok = false;
-                        break;
+                    tma_load_2d(smem + Cfg::OFF_A + box * (kBM * 32 * 4), &tmA, (int32_t)(mt * kBM),
+                                (int32_t)(box * 32), a_full, pol_a);
+                for (int64_t t = t0; t < t1 && ok; ++t) {
+                    for (int c = 0; c < KC; ++c, ++gq) {
+                        const int sb = (int)(gq % NB);
+                        if (gq >= NB && !mbar_wait_bounded(&b_empty[sb], (uint32_t)((gq / NB) & 1) ^ 1)) {
+                            ok = false;
+                            break;
+                        }
+                        mbar_arrive_expect_tx(&b_full[sb], Cfg::B_CHUNK);
+                        bulk_load(smem + Cfg::OFF_B + sb * Cfg::B_CHUNK,
+                                  Bp + t * Cfg::B_TILE + c * Cfg::B_CHUNK, Cfg::B_CHUNK, &b_full[sb], pol_b);
                     }
-                    mbar_arrive_expect_tx(&b_full[sb], Cfg::B_TILE);
-                    bulk_load(smem + Cfg::OFF_B + sb * Cfg::B_TILE, Bp + t * Cfg::B_TILE, Cfg::B_TILE,
-                              &b_full[sb], pol_b);
                 }
             }
             if (!ok) atomicOr(status, kDevErrTimeout);
+            // copies still in flight land before the block may exit
+            if (j >= 1) mbar_wait_bounded(a_full, (uint32_t)((j - 1) & 1));
+            for (int64_t q = gq > NB ? gq - NB : 0; q < gq; ++q)
+                mbar_wait_bounded(&b_full[q % NB], (uint32_t)((q / NB) & 1));
         }
+        return;
+    }
+
+    if (warp == 14) {
+        // ------------------------------------------------ C0 loader
+        if (!use_c0) return;
+        const uint64_t pol_c = policy_evict_first();
+        const float *C = static_cast<const float *>(a.C);
+        int64_t q = 0;  // sub-tiles issued
+        bool ok = true;
+        for (int64_t item = blockIdx.x; item < total && ok; item += gridDim.x) {
+            const int64_t mt = item / nch;
+            const int64_t t0 = (item % nch) * rnch;
+            const int64_t t1 = (t0 + rnch < ntiles) ? t0 + rnch : ntiles;
+            for (int64_t t = t0; t < t1 && ok; ++t) {
+                for (int sub = 0; sub < kRSUBS; ++sub, ++q) {
+                    const int st = (int)(q % CS);
+                    if (q >= CS && !warp_wait(&c_empty[st], (uint32_t)((q / CS) & 1) ^ 1)) {
+                        ok = false;
+                        break;
+                    }
+                    float *slot = cslots + st * (kBM * kRSUB);
+                    const int64_t col0 = t * NT + sub * kRSUB;
+                    if (c_tma) {
+                        if (lane == 0) {
+                            mbar_arrive_expect_tx(&c_full[st], Cfg::SLOT);
+                            tma_load_2d(slot, &tmC, (int32_t)(mt * kBM), (int32_t)col0, &c_full[st], pol_c);
+                        }
+                    } else {
+                        // element e of the slot is (row e % 128, column e / 128)
+                        for (int e = lane; e < kBM * kRSUB; e += 32) {
+                            const int64_t row = mt * kBM + (e & (kBM - 1));
+                            const int64_t col = col0 + e / kBM;
+                            const bool in = row < a.m && col < a.n;
+                            cp_async4(slot + e, in ? C + row + col * a.ldc : C, in ? 4u : 0u);
+                        }
+                        cp_async_mbar_arrive(&c_full[st]);
+                    }
+                }
+            }
+        }
+        if (!ok && lane == 0) atomicOr(status, kDevErrTimeout);
+        if (!c_tma) asm volatile("cp.async.wait_all;" ::: "memory");
+        if (lane == 0)
+            for (int64_t r = q > CS ? q - CS : 0; r < q; ++r)
+                mbar_wait_bounded(&c_full[r % CS], (uint32_t)((r / CS) & 1));
+        return;
+    }
+
+    if (warp == 15) {
+        // ------------------------------------------------ storer (TMA mode)
+        if (!c_tma || lane != 0) return;
+        int64_t q = 0;  // sub-tiles stored
+        bool ok = true;
+        for (int64_t item = blockIdx.x; item < total && ok; item += gridDim.x) {
+            const int64_t mt = item / nch;
+            const int64_t t0 = (item % nch) * rnch;
+            const int64_t t1 = (t0 + rnch < ntiles) ? t0 + rnch : ntiles;
+            for (int64_t t = t0; t < t1 && ok; ++t) {
+                for (int sub = 0; sub < kRSUBS; ++sub, ++q) {
+                    const int st = (int)(q % CS);
+                    if (!mbar_wait_bounded(&c_store[st], (uint32_t)((q / CS) & 1))) {
+                        ok = false;
+                        break;
+                    }
+                    const int64_t col0 = t * NT + sub * kRSUB;
+                    if (col0 < a.n)  // boxes wholly past the last column are not issued
+                        tma_store_2d(&tmC, cslots + st * (kBM * kRSUB), (int32_t)(mt * kBM), (int32_t)col0);
+                    bulk_commit();
+                    bulk_wait_read_all();
+                    mbar_arrive(&c_empty[st]);
+                }
+            }
+        }
+        if (!ok) atomicOr(status, kDevErrTimeout);
+        bulk_wait_all();
         return;
     }
 
@@ -578,31 +758,34 @@ __global__ void __launch_bounds__(448, 1)
         // ------------------------------------------------ MMA issuer
         if (lane == 0) {
             constexpr uint32_t idesc = umma_idesc(kBM, NT);
-            int64_t g = 0;
+            int64_t g = 0, gq = 0;
             int j = 0;
             bool ok = true;
             for (int64_t item = blockIdx.x; item < total && ok; item += gridDim.x, ++j) {
-                const int64_t t0 = (item % nch) * kRNCH;
-                const int64_t t1 = (t0 + kRNCH < ntiles) ? t0 + kRNCH : ntiles;
+                const int64_t t0 = (item % nch) * rnch;
+                const int64_t t1 = (t0 + rnch < ntiles) ? t0 + rnch : ntiles;
                 if (!mbar_wait_bounded(a_conv, (uint32_t)(j & 1))) {
                     ok = false;
                     break;
                 }
                 tc_fence_after();
-                for (int64_t t = t0; t < t1; ++t, ++g) {
-                    const int sb = (int)(g & 1);
-                    if (!mbar_wait_bounded(&b_full[sb], (uint32_t)((g >> 1) & 1)) ||
-                        (g >= 2 && !mbar_wait_bounded(&tempty[sb], (uint32_t)((g >> 1) & 1) ^ 1))) {
+                for (int64_t t = t0; t < t1 && ok; ++t, ++g) {
+                    const int tb = (int)(g & 1);
+                    if (g >= 2 && !mbar_wait_bounded(&tempty[tb], (uint32_t)((g >> 1) & 1) ^ 1)) {
                         ok = false;
                         break;
                     }
-                    tc_fence_after();
-                    const uint32_t tacc = tmem + (uint32_t)(sb * NT);
-#pragma unroll
-                    for (int c = 0; c < KC; ++c) {
-                        const uint32_t ahi = smem_addr(smem + c * (kBM * kKB * 4));
+                    const uint32_t tacc = tmem + (uint32_t)(tb * NT);
+                    for (int c = 0; c < KC; ++c, ++gq) {
+                        const int sb = (int)(gq % NB);
+                        if (!mbar_wait_bounded(&b_full[sb], (uint32_t)((gq / NB) & 1))) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        const uint32_t ahi = smem_addr(smem + Cfg::OFF_A + c * (kBM * kKB * 4));
                         const uint32_t alo = ahi + kBM * kKB * 2;
-                        const uint32_t bhi = smem_addr(smem + Cfg::OFF_B + sb * Cfg::B_TILE + c * (2 * NT * kKB * 2));
+                        const uint32_t bhi = smem_addr(smem + Cfg::OFF_B + sb * Cfg::B_CHUNK);
                         const uint32_t blo = bhi + NT * kKB * 2;
 #pragma unroll
                         for (int ks = 0; ks < kKB / 16; ++ks) {
@@ -612,9 +795,9 @@ __global__ void __launch_bounds__(448, 1)
                             umma_bf16(tacc, umma_desc(ahi + off), umma_desc(blo + off), idesc, 1u);
                             umma_bf16(tacc, umma_desc(alo + off), umma_desc(bhi + off), idesc, 1u);
                         }
+                        umma_commit(&b_empty[sb]);
                     }
-                    umma_commit(&b_empty[sb]);
-                    umma_commit(&tfull[sb]);
+                    if (ok) umma_commit(&tfull[tb]);
                 }
                 if (ok) umma_commit(a_empty);
             }
@@ -647,7 +830,7 @@ __global__ void __launch_bounds__(448, 1)
             }
 #pragma unroll
             for (int c = 0; c < KC; ++c) {
-                unsigned char *stage = smem + c * (kBM * kKB * 4);
+                unsigned char *stage = smem + Cfg::OFF_A + c * (kBM * kKB * 4);
                 const float *src = reinterpret_cast<const float *>(stage);  // [64][128] FP32
                 float x[kKB];
 #pragma unroll
@@ -681,71 +864,80 @@ __global__ void __launch_bounds__(448, 1)
     }
 
     // ---------------------------------------------------- epilogue (warps 6-13)
+    // Each warp decides on its own to stop after a timed-out wait: the only
+    // named barrier it meets afterwards is the final one with warp 5.
     const int quarter = warp % 4;
-    const int half = (warp - 6) / 4;
+    const int half = (warp - 6) / 4;  // columns half*64 .. half*64+63 of each tile
     const float alpha = static_cast<float>(a.alpha);
     const float beta = static_cast<float>(a.beta);
     float *C = static_cast<float *>(a.C);
-    int64_t g = 0;
-    bool stop = false;
-    for (int64_t item = blockIdx.x; item < total && !stop; item += gridDim.x) {
+    int64_t g = 0, gc = 0;
+    bool ok = true;
+    for (int64_t item = blockIdx.x; item < total && ok; item += gridDim.x) {
         const int64_t mt = item / nch;
-        const int64_t t0 = (item % nch) * kRNCH;
-        const int64_t t1 = (t0 + kRNCH < ntiles) ? t0 + kRNCH : ntiles;
+        const int64_t t0 = (item % nch) * rnch;
+        const int64_t t1 = (t0 + rnch < ntiles) ? t0 + rnch : ntiles;
         const int64_t i = mt * kBM + quarter * 32 + lane;
-        for (int64_t t = t0; t < t1; ++t, ++g) {
+        float *crow = C + i;
+        for (int64_t t = t0; t < t1 && ok; ++t, ++g, gc += kRSUBS) {
             const int tb = (int)(g & 1);
-            const bool got = mbar_wait_bounded(&tfull[tb], (uint32_t)((g >> 1) & 1));
-            if (!got && lane == 0) atomicOr(ep_abort, 1u);
-            named_barrier(3, 256);
-            stop = *ep_abort != 0u;
-            named_barrier(3, 256);
-            if (stop) {
-                if (warp == 6 && lane == 0) atomicOr(status, kDevErrTimeout);
+            if (!warp_wait(&tfull[tb], (uint32_t)((g >> 1) & 1))) {
+                ok = false;
                 break;
             }
             tc_fence_after();
-            const int64_t j0 = t * NT + half * 64;
-            float *crow = C + i;
-            // all 64 C0 loads of this thread's half row are issued before any
-            // store: 64 KB of reads in flight per SM keep HBM busy
-            float c0v[64];
-            if (beta != 0.f && i < a.m) {
+            float acc[64];
+            tmem_ld64(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(tb * NT + half * 64), acc);
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty[tb]);  // the accumulator may be refilled
 #pragma unroll
-                for (int jj = 0; jj < 64; ++jj)
-                    c0v[jj] = (j0 + jj < a.n) ? crow[(j0 + jj) * a.ldc] : 0.f;
-            }
-#pragma unroll
-            for (int b = 0; b < 4; ++b) {
-                float acc[16];
-                tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(tb * NT + half * 64 + b * 16),
-                          acc);
-                if (b == 3) {
-                    tc_fence_before();
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(&tempty[tb]);  // the accumulator may be refilled
+            for (int h = 0; h < 2; ++h) {
+                float *v = acc + h * 32;
+                const int64_t q = gc + half * 2 + h;  // this sub-tile's ring index
+                const int st = (int)(q % CS);
+                const uint32_t par = (uint32_t)((q / CS) & 1);
+                float *slot = cslots + st * (kBM * kRSUB) + quarter * 32 + lane;  // column 0, own row
+                if (use_c0 ? !warp_wait(&c_full[st], par)
+                           : (c_tma && q >= CS && !warp_wait(&c_empty[st], par ^ 1))) {
+                    ok = false;
+                    break;
                 }
-                if (i < a.m) {
 #pragma unroll
-                    for (int jj = 0; jj < 16; ++jj) {
-                        const int64_t jc = j0 + b * 16 + jj;
-                        if (jc < a.n) {
-                            float o = (alpha == 1.f) ? acc[jj] : alpha * acc[jj];
-                            if (beta != 0.f) o = fmaf(beta, c0v[b * 16 + jj], o);
-                            crow[jc * a.ldc] = o;
-                        }
+                for (int jj = 0; jj < 32; ++jj) {
+                    v[jj] = alpha * v[jj];
+                    if (use_c0) v[jj] = fmaf(beta, slot[jj * kBM], v[jj]);
+                }
+                if (c_tma) {
+                    // result replaces C0 in the slot; the storer writes it out
+#pragma unroll
+                    for (int jj = 0; jj < 32; ++jj) slot[jj * kBM] = v[jj];
+                    fence_proxy_async_smem();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&c_store[st]);
+                } else {
+                    if (use_c0) {
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(&c_empty[st]);
+                    }
+                    const int64_t jb = t * NT + half * 64 + h * 32;
+                    if (i < a.m) {
+#pragma unroll
+                        for (int jj = 0; jj < 32; ++jj)
+                            if (jb + jj < a.n) crow[(jb + jj) * a.ldc] = v[jj];
                     }
                 }
             }
         }
     }
+    if (!ok && lane == 0) atomicOr(status, kDevErrTimeout);
     tc_fence_before();
     named_barrier(2, 288);  // with warp 5, before it frees TMEM
 }
 
 template <int KC>
-static cudaError_t launch_rx3_t(const CUtensorMap *tmA, const RankArgs &a, unsigned *status,
-                                cudaStream_t s) {
+static cudaError_t launch_rx3_t(const CUtensorMap *tmA, const CUtensorMap *tmC, const RankArgs &a,
+                                unsigned *status, cudaStream_t s) {
     using Cfg = RX3Cfg<KC>;
     static bool attr_done = false;
     if (!attr_done) {
@@ -756,17 +948,26 @@ static cudaError_t launch_rx3_t(const CUtensorMap *tmA, const RankArgs &a, unsig
     }
     const int64_t mtiles = (a.m + kBM - 1) / kBM;
     const int64_t ntiles = (a.n + Cfg::NT - 1) / Cfg::NT;
-    const int64_t items = mtiles * ((ntiles + kRNCH - 1) / kRNCH);
     const int64_t slots = a.num_sms > 0 ? a.num_sms : 1;
+    // n-tiles per item: long items amortise the A tile's load and split, but
+    // keep at least ~4 items per block for balance
+    int64_t rnch = mtiles * ntiles / (4 * slots);
+    rnch = rnch < 1 ? 1 : (rnch > kRNCHMax ? kRNCHMax : rnch);
+    const int64_t items = mtiles * ((ntiles + rnch - 1) / rnch);
     const unsigned grid = (unsigned)(items < slots ? items : slots);
     if (grid == 0) return cudaSuccess;
-    rankk_bf16x3_kernel<KC><<<grid, Cfg::THREADS, Cfg::SMEM, s>>>(*tmA, a, status);
+    CUtensorMap none;
+    memset(&none, 0, sizeof(none));
+    const int smem = (tmC || a.beta != 0.0) ? Cfg::SMEM : Cfg::SMEM_NO_SLOTS;
+    rankk_bf16x3_kernel<KC><<<grid, Cfg::THREADS, smem, s>>>(*tmA, tmC ? *tmC : none, a, status,
+                                                             tmC ? 1 : 0, (int)rnch);
     return cudaGetLastError();
 }
 
-cudaError_t launch_rankk_bf16x3(const CUtensorMap *tmA, const RankArgs &a, unsigned *status,
-                                cudaStream_t s) {
-    return a.kp <= kKB ? launch_rx3_t<1>(tmA, a, status, s) : launch_rx3_t<2>(tmA, a, status, s);
+cudaError_t launch_rankk_bf16x3(const CUtensorMap *tmA, const CUtensorMap *tmC, const RankArgs &a,
+                                unsigned *status, cudaStream_t s) {
+    return a.kp <= kKB ? launch_rx3_t<1>(tmA, tmC, a, status, s)
+                       : launch_rx3_t<2>(tmA, tmC, a, status, s);
 }
 
 }  // namespace tsmm

@@ -148,9 +148,13 @@ cudaError_t launch_tall_bf16x3(int np, const CUtensorMap *tmap, const TallArgs &
 cudaError_t launch_pack_b_bf16x3(int64_t k, int64_t n, const void *B, int64_t ldb, void *dst, int np,
                                  int64_t nchunks, int64_t ntiles, cudaStream_t s);
 // Regime (ii) in the BF16x3 mode: tile width of its packed B, and the kernel.
+// tmC: tensor map of C (box 128 x kX3RankSub) when C meets the TMA rules
+// (C0 loads and C stores by TMA), else nullptr (C0 by 4-byte cp.async, C by
+// plain stores).
 constexpr int kX3RankNT = 128;
-cudaError_t launch_rankk_bf16x3(const CUtensorMap *tmA, const RankArgs &a, unsigned *status,
-                                cudaStream_t s);
+constexpr int kX3RankSub = 32;
+cudaError_t launch_rankk_bf16x3(const CUtensorMap *tmA, const CUtensorMap *tmC, const RankArgs &a,
+                                unsigned *status, cudaStream_t s);
 
 // Process-wide plan cache (tsmm_tune.cu): tuned split counts keyed by
 // (dtype, m, n, k, SM count).  Lookup returns 0 when absent.

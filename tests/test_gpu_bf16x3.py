@@ -151,7 +151,13 @@ def test_bf16x3_full_size_sampled():
 
 
 @pytest.mark.parametrize("m,n,k,beta", [(1000, 300, 64, 1.0), (2050, 1000, 128, 1.0), (515, 129, 33, 0.0),
-                                        (4096, 2048, 100, -0.5), (300, 5000, 16, 1.0)])
+                                        (4096, 2048, 100, -0.5), (300, 5000, 16, 1.0),
+                                        # beta = 0: plain stores (ldc*4 not a multiple of 16)
+                                        (2050, 1000, 128, 0.0),
+                                        # beta = 0 with TMA stores; C starts as NaN
+                                        (1024, 1000, 100, 0.0),
+                                        # items of 6 n-tiles, the last chunk ragged
+                                        (8192, 8000, 72, 1.0)])
 def test_bf16x3_rankk_integer_bit_exact(m, n, k, beta):
     """Regime (ii) in the tensor-core mode: integer inputs are exact."""
     A = ti.matrix_np(m, k, 61, "integer", np.float32)
@@ -161,6 +167,30 @@ def test_bf16x3_rankk_integer_bit_exact(m, n, k, beta):
     assert pl.info()["regime"] == 2
     Cref, _ = oracle.tsmm(1.5, A, B, beta, C0 if beta else None)
     np.testing.assert_array_equal(C, oracle.round_to(Cref, np.float32))
+
+
+@pytest.mark.parametrize("beta", [1.5, 0.0])
+@pytest.mark.parametrize("ldc_pad,c_offset", [(0, 0), (4, 0), (1, 0), (0, 1), (12, 3)])
+def test_bf16x3_rankk_c_layouts(ldc_pad, c_offset, beta):
+    """C0 loads and C stores go through TMA when C's base and column stride
+    are 16-byte aligned, else through 4-byte cp.async and plain stores; both
+    give the exact result, and padding rows of C stay untouched."""
+    m, n, k = 1028, 700, 96
+    A = ti.matrix_np(m, k, 64, "integer", np.float32)
+    B = ti.matrix_np(k, n, 65, "integer", np.float32)
+    C0 = ti.matrix_np(m, n, 66, "integer", np.float32)
+    dA = to_device(A, m)
+    pb = tsmm.pack_b(to_device(B), precision=X3)
+    pl = tsmm.plan(m, n, k, torch.float32, precision=X3)
+    ldc = m + ldc_pad
+    dC = to_device(C0, ldc, c_offset)
+    tsmm.execute(pl, -2.0, dA, pb, beta, dC)
+    pl.check()
+    Cref, _ = oracle.tsmm(-2.0, A, B, beta, C0 if beta else None)
+    np.testing.assert_array_equal(dC.cpu().numpy(), oracle.round_to(Cref, np.float32))
+    if ldc_pad:
+        full = torch.as_strided(dC, (ldc, n), (1, ldc)).cpu().numpy()
+        assert np.all(np.isnan(full[m:, :]))
 
 
 @pytest.mark.parametrize("m,n,k", [(2000, 1500, 128), (1000, 700, 64)])

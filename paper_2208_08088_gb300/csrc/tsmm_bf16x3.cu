@@ -473,7 +473,9 @@ cudaError_t launch_pack_b_bf16x3(int64_t k, int64_t n, const void *B, int64_t ld
 //               alpha*acc + beta*C0;
 //   warp 14     C0 loader (beta != 0): 128 x 32 sub-tiles of C0 into a ring
 //               of CS shared-memory slots;
-//   warp 15     storer: TMA stores of finished sub-tiles from their slots.
+//   warp 15     storer: TMA stores of finished sub-tiles from their slots; a
+//               slot is freed once its store has read it (`lag` = 1 keeps
+//               the newest store in flight while freeing the one before).
 // When C meets the TMA rules (16-byte aligned base and column stride) each
 // sub-tile lives in one slot from C0 load to C store: the epilogue overwrites
 // C0 with the result in place, the storer writes it out by TMA and frees the
@@ -494,6 +496,11 @@ struct RX3Cfg {
     static constexpr int B_TILE = KC * B_CHUNK;
     static constexpr int NB = KC == 1 ? 2 : 3;         // B chunk buffers
     static constexpr int CS = KC == 1 ? 8 : 4;         // C slots
+    // Slot q % CS must always serve the same epilogue half (sub-tile q % 4):
+    // its consumers then meet its phases in order, so parity waits cannot
+    // alias (a half two phases ahead of a slot shared with the other half
+    // would see the slot's older phase as complete).
+    static_assert(CS % kRSUBS == 0, "each slot serves one epilogue half");
     static constexpr int SLOT = kBM * kRSUB * 4;
     static constexpr int OFF_BAR = 0;                  // barriers first
     static constexpr int OFF_A = 1024;
@@ -533,6 +540,10 @@ __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.comm
 __device__ __forceinline__ void bulk_wait_read_all() {
     asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
 }
+// every committed store but the newest has finished reading shared memory
+__device__ __forceinline__ void bulk_wait_read_but_one() {
+    asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+}
 // every committed store is complete
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
@@ -571,7 +582,7 @@ __device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity) {
 template <int KC>
 __global__ void __launch_bounds__(512, 1)
     rankk_bf16x3_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmC,
-                        const RankArgs a, unsigned *status, int c_tma, int rnch) {
+                        const RankArgs a, unsigned *status, int c_tma, int rnch, int lag) {
     using Cfg = RX3Cfg<KC>;
     constexpr int NT = Cfg::NT;
     constexpr int NB = Cfg::NB;
@@ -744,8 +755,13 @@ __global__ void __launch_bounds__(512, 1)
                     if (col0 < a.n)  // boxes wholly past the last column are not issued
                         tma_store_2d(&tmC, cslots + st * (kBM * kRSUB), (int32_t)(mt * kBM), (int32_t)col0);
                     bulk_commit();
-                    bulk_wait_read_all();
-                    mbar_arrive(&c_empty[st]);
+                    if (lag == 0) {
+                        bulk_wait_read_all();
+                        mbar_arrive(&c_empty[st]);
+                    } else if (q >= 1) {
+                        bulk_wait_read_but_one();
+                        mbar_arrive(&c_empty[(q - 1) % CS]);
+                    }
                 }
             }
         }
@@ -959,8 +975,10 @@ static cudaError_t launch_rx3_t(const CUtensorMap *tmA, const CUtensorMap *tmC, 
     CUtensorMap none;
     memset(&none, 0, sizeof(none));
     const int smem = (tmC || a.beta != 0.0) ? Cfg::SMEM : Cfg::SMEM_NO_SLOTS;
+    // with only 4 slots and C0 to prefetch, free each slot as early as possible
+    const int lag = (KC == 2 && a.beta != 0.0) ? 0 : 1;
     rankk_bf16x3_kernel<KC><<<grid, Cfg::THREADS, smem, s>>>(*tmA, tmC ? *tmC : none, a, status,
-                                                             tmC ? 1 : 0, (int)rnch);
+                                                             tmC ? 1 : 0, (int)rnch, lag);
     return cudaGetLastError();
 }
 

@@ -113,7 +113,7 @@ __global__ void __launch_bounds__(TallCfg<T, NP>::THREADS, 2)
     const int wk = warp / Cfg::WM;
     const int gl = lane / Cfg::LR;
     const int lr = lane % Cfg::LR;
-    const int rloc = wm * Cfg::WROWS + lr * Cfg::R;
+    const int rloc = wm * Cfg::WROWS + lr * Cfg::RV;
     const int cloc = gl * Cfg::CN;
     int64_t g = 0;
     for (int64_t item = blockIdx.x; item < gp.total_items; item += gridDim.x) {
@@ -139,7 +139,7 @@ __global__ void __launch_bounds__(TallCfg<T, NP>::THREADS, 2)
 #pragma unroll
             for (int c = 0; c < Cfg::KPW; ++c) {
                 const int col = wk * Cfg::KPW + c;
-                const Vec<T, Cfg::R> av = ld_vec<T, Cfg::R>(As + col * Cfg::BM + rloc);
+                const Vec<T, Cfg::R> av = tall_load_rows<Cfg, T>(As + col * Cfg::BM, rloc);
                 acc.fma_column(av, Bs + col * NP + cloc);
             }
             __syncwarp();
@@ -158,7 +158,7 @@ __global__ void __launch_bounds__(TallCfg<T, NP>::THREADS, 2)
             Vec<T, Cfg::R> v;
 #pragma unroll
             for (int r = 0; r < Cfg::R; ++r) v.v[r] = acc.get(r, c);
-            st_vec<T, Cfg::R>(red + (wk * NP + cloc + c) * Cfg::BM + rloc, v);
+            tall_store_rows<Cfg, T>(red + (wk * NP + cloc + c) * Cfg::BM, rloc, v);
         }
         named_barrier(1, Cfg::CONSUMERS);
         tall_finish<T, NP>(red, a, slab, split, threadIdx.x, flag);

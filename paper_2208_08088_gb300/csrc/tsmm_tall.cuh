@@ -33,11 +33,23 @@ namespace tsmm {
 template <typename T, int NP>
 struct TallCfg {
     static constexpr int VEC = 16 / (int)sizeof(T);   // elements per 16-byte vector
-    static constexpr int R = VEC;                      // rows per thread
-    static constexpr int CN = NP < 16 ? NP : 16;       // columns per thread
+    // The FMA-bound FP32 shapes (n >= 32) use 8 x 8 thread tiles: 32 packed
+    // fmas per 4 shared-memory loads of 16 bytes (a 16-byte load costs four
+    // shared-memory wavefronts whatever its address pattern, and the 4 x 16
+    // tile's 5 loads per 32 fmas saturate them before the FMA pipe).  A
+    // thread's 8 rows are two groups of 4, half a warp tile apart, so the
+    // lanes along m read adjacent 16-byte words of A (no bank shared).
+    static constexpr bool WIDE = sizeof(T) == 4 && NP >= 32;
+    static constexpr int R = WIDE ? 8 : VEC;                  // rows per thread
+    static constexpr int CN = WIDE ? 8 : (NP < 16 ? NP : 16);  // columns per thread
     static constexpr int G = NP / CN;                  // lane groups along n
     static constexpr int LR = 32 / G;                  // lanes along m
     static constexpr int WROWS = LR * R;               // rows per warp
+    static constexpr int RG = WIDE ? 2 : 1;            // row groups per thread
+    static constexpr int RV = R / RG;                  // rows per group (one vector)
+    static constexpr int GSTRIDE = WROWS / RG;         // distance between a thread's groups
+    // local row of this thread's row r, given rloc = wm*WROWS + lr*RV
+    static __host__ __device__ constexpr int row(int rloc, int r) { return rloc + (r / RV) * GSTRIDE + r % RV; }
     static constexpr int BM = (sizeof(T) == 4) ? 128 : 64;
     static constexpr int WM = BM / WROWS;              // warps along m
     static constexpr int NWARPS = kTallConsumerWarps;
@@ -67,6 +79,30 @@ struct TallCfg {
     static_assert(WK * KPW == BKS, "stage split");
     static_assert(BM * (int)sizeof(T) % 16 == 0, "TMA box row bytes");
 };
+
+// A thread's R rows of one A column (cb: the column's first element) and
+// the store of R row values of one C column, in the thread's row layout.
+template <typename Cfg, typename T>
+__device__ __forceinline__ Vec<T, Cfg::R> tall_load_rows(const T *cb, int rloc) {
+    Vec<T, Cfg::R> v;
+#pragma unroll
+    for (int gi = 0; gi < Cfg::RG; ++gi) {
+        const Vec<T, Cfg::RV> part = ld_vec<T, Cfg::RV>(cb + rloc + gi * Cfg::GSTRIDE);
+#pragma unroll
+        for (int r = 0; r < Cfg::RV; ++r) v.v[gi * Cfg::RV + r] = part.v[r];
+    }
+    return v;
+}
+template <typename Cfg, typename T>
+__device__ __forceinline__ void tall_store_rows(T *cb, int rloc, const Vec<T, Cfg::R> &v) {
+#pragma unroll
+    for (int gi = 0; gi < Cfg::RG; ++gi) {
+        Vec<T, Cfg::RV> part;
+#pragma unroll
+        for (int r = 0; r < Cfg::RV; ++r) part.v[r] = v.v[gi * Cfg::RV + r];
+        st_vec<T, Cfg::RV>(cb + rloc + gi * Cfg::GSTRIDE, part);
+    }
+}
 
 // Sum of the WK per-warp partial tiles, then store / split-K finish.
 // `red` holds WK tiles laid out [WK][NP][BM]; on return red[0..NP*BM) is reused.
@@ -291,7 +327,7 @@ __global__ void __launch_bounds__(TallCfg<T, NP>::THREADS, TallCfg<T, NP>::RESID
     const int wk = warp / Cfg::WM;
     const int g = lane / Cfg::LR;
     const int lr = lane % Cfg::LR;
-    const int rloc = wm * Cfg::WROWS + lr * Cfg::R;  // first local row of this thread
+    const int rloc = wm * Cfg::WROWS + lr * Cfg::RV;  // first local row of this thread
     const int cloc = g * Cfg::CN;                    // first column of this thread
 
     typename TallAcc<T, NP>::type acc;
@@ -309,7 +345,7 @@ __global__ void __launch_bounds__(TallCfg<T, NP>::THREADS, TallCfg<T, NP>::RESID
 #pragma unroll
         for (int c = 0; c < Cfg::KPW; ++c) {
             const int col = wk * Cfg::KPW + c;
-            const Vec<T, Cfg::R> av = ld_vec<T, Cfg::R>(As + col * Cfg::BM + rloc);
+            const Vec<T, Cfg::R> av = tall_load_rows<Cfg, T>(As + col * Cfg::BM, rloc);
             acc.fma_column(av, Bs + col * NP + cloc);
         }
         __syncwarp();
@@ -330,7 +366,7 @@ __global__ void __launch_bounds__(TallCfg<T, NP>::THREADS, TallCfg<T, NP>::RESID
         Vec<T, Cfg::R> v;
 #pragma unroll
         for (int r = 0; r < Cfg::R; ++r) v.v[r] = acc.get(r, c);
-        st_vec<T, Cfg::R>(red + (wk * NP + cloc + c) * Cfg::BM + rloc, v);
+        tall_store_rows<Cfg, T>(red + (wk * NP + cloc + c) * Cfg::BM, rloc, v);
     }
     named_barrier(1, Cfg::CONSUMERS);
     tall_finish<T, NP>(red, a, slab, split, threadIdx.x, flag);
@@ -356,9 +392,9 @@ __global__ void __launch_bounds__(TallCfg<T, NP>::CONSUMERS, 2)
     const int wk = warp / Cfg::WM;
     const int g = lane / Cfg::LR;
     const int lr = lane % Cfg::LR;
-    const int rloc = wm * Cfg::WROWS + lr * Cfg::R;
+    const int rloc = wm * Cfg::WROWS + lr * Cfg::RV;
     const int cloc = g * Cfg::CN;
-    const int64_t i0 = slab * Cfg::BM + rloc;
+    const int64_t i0 = slab * Cfg::BM;
     const T *A = static_cast<const T *>(a.A);
     const T *Bp = static_cast<const T *>(a.Bp);
 
@@ -371,8 +407,10 @@ __global__ void __launch_bounds__(TallCfg<T, NP>::CONSUMERS, 2)
             if (p >= k1) break;
             Vec<T, Cfg::R> av;
 #pragma unroll
-            for (int r = 0; r < Cfg::R; ++r)
-                av.v[r] = (i0 + r < a.m) ? A[i0 + r + p * a.lda] : T(0);
+            for (int r = 0; r < Cfg::R; ++r) {
+                const int64_t i = i0 + Cfg::row(rloc, r);
+                av.v[r] = (i < a.m) ? A[i + p * a.lda] : T(0);
+            }
             acc.fma_column(av, Bp + p * NP + cloc);
         }
     }
@@ -381,7 +419,7 @@ __global__ void __launch_bounds__(TallCfg<T, NP>::CONSUMERS, 2)
         Vec<T, Cfg::R> v;
 #pragma unroll
         for (int r = 0; r < Cfg::R; ++r) v.v[r] = acc.get(r, c);
-        st_vec<T, Cfg::R>(red + (wk * NP + cloc + c) * Cfg::BM + rloc, v);
+        tall_store_rows<Cfg, T>(red + (wk * NP + cloc + c) * Cfg::BM, rloc, v);
     }
     named_barrier(1, Cfg::CONSUMERS);
     tall_finish<T, NP>(red, a, slab, split, threadIdx.x, flag);

@@ -133,8 +133,8 @@ def test_alpha_zero_reads_neither_A_nor_B(dtype, n, k):
 
 @pytest.mark.parametrize("dtype", DT)
 @pytest.mark.parametrize("n,k", [(16, 100), (200, 64)])
-def test_beta_zero_overwrites_nan(dtype, n, k):
-    m = 150
+@pytest.mark.parametrize("m", [150, 152])  # 152: C meets the TMA rules
+def test_beta_zero_overwrites_nan(dtype, n, k, m):
     A, B, _ = gen(m, n, k, dtype)
     C, _, _ = run(A, B, None, 2.0, 0.0)
     assert np.all(np.isfinite(C))
@@ -256,10 +256,12 @@ def test_plan_reuse_across_A_pointers():
 @pytest.mark.parametrize("dtype", DT)
 @pytest.mark.parametrize("k", [3, 16, 32, 33, 100])
 @pytest.mark.parametrize("beta", [0.0, 1.0, -0.5])
-def test_rankk_persistent_many_tiles(dtype, k, beta):
+@pytest.mark.parametrize("m", [2050, 2048])
+def test_rankk_persistent_many_tiles(dtype, k, beta, m):
     """More tiles than resident blocks: every block walks several tiles, reusing
-    its k-chunk ring and (k <= 32, beta != 0) its two C0 buffers."""
-    m, n = 2050, 1000
+    its k-chunk ring and its C buffers (m = 2048: C meets the TMA rules, so C0
+    and C move by tensor copies; m = 2050: plain loads and stores)."""
+    n = 1000
     A, B, C0 = gen(m, n, k, dtype)
     C, pl, _ = run(A, B, C0 if beta != 0 else None, 1.0 if k != 33 else 0.75, beta)
     assert pl.info()["regime"] == 2

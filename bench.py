@@ -540,10 +540,17 @@ def run_e2e(args, tsmm, torch, tdt, es, pts, A, packed, plans, world):
 
     run(2)  # warm-up
     torch.cuda.synchronize()
-    if world > 1:
-        torch.distributed.barrier()
+    # the host link's own rate at this moment (one upload of A, nothing else running)
+    key0 = next(iter(hostA))
     a = torch.cuda.Event(enable_timing=True)
     b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    devA[0][key0].copy_(hostA[key0], non_blocking=True)
+    b.record(stream)
+    torch.cuda.synchronize()
+    link_gbs = hostA[key0].numel() * es / (a.elapsed_time(b) * 1e-3) / 1e9
+    if world > 1:
+        torch.distributed.barrier()
     a.record(stream)
     run(steps)
     b.record(stream)
@@ -557,7 +564,7 @@ def run_e2e(args, tsmm, torch, tdt, es, pts, A, packed, plans, world):
     del hostA, devA, devC
     return {"value": round(world * fl * steps / (ms * 1e-3) / 1e9, 1), "unit": UNIT,
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": steps,
-            "ms_per_step": round(ms / steps, 3),
+            "ms_per_step": round(ms / steps, 3), "host_to_device_gbs": round(link_gbs, 1),
             "pipeline": "inputs double-buffered on a copy stream: step s+1's upload overlaps step s"}
 
 

@@ -387,6 +387,21 @@ TSMM_API tsmm_status tsmm_execute_noalloc(tsmm_dtype dtype, int64_t m, int64_t n
                                           const void *B_dev, int64_t ldb, double beta,
                                           void *C_dev, int64_t ldc, tsmm_stream_t stream);
 
+/*
+ * tsmm_diag_bounded_wait -- diagnostics for the failure path (no counterpart
+ * in the paper).  Every wait on an mbarrier in the library's kernels gives up
+ * after one second (or 2^24 polls) and, if the phase never completed, records
+ * TSMM_ERR_TIMEOUT in a device status word and lets the kernel return.  This
+ * entry point runs that same wait, with at most `polls` polls, against a
+ * barrier that nothing completes, in one block of one warp, synchronously.
+ * Returns TSMM_ERR_TIMEOUT when the wait ran out (the expected outcome),
+ * TSMM_OK if the phase was seen complete, INVALID_ARG for polls == 0, CUDA on
+ * an allocation, launch or copy error.  *cycles_out (may be NULL): SM clock
+ * cycles the wait took; *seconds_out (may be NULL): the same at the device's
+ * maximum SM clock.  Allocates and frees 16 bytes of device memory.
+ */
+TSMM_API tsmm_status tsmm_diag_bounded_wait(uint32_t polls, uint64_t *cycles_out, double *seconds_out);
+
 #ifdef __cplusplus
 }
 #endif

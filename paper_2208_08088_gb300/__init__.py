@@ -142,6 +142,9 @@ def _load():
     L.tsmm_plan_cache_clear.argtypes = []
     L.tsmm_plan_cache_size.restype = i64
     L.tsmm_plan_cache_size.argtypes = []
+    L.tsmm_diag_bounded_wait.restype = ci
+    L.tsmm_diag_bounded_wait.argtypes = [ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint64),
+                                         ctypes.POINTER(dbl)]
     return L
 
 
@@ -397,6 +400,16 @@ def execute_grouped(problems, stream=None) -> None:
         items.append((p.handle, alpha, A.data_ptr() if A.numel() else 0, lda, pb.handle, beta,
                       C.data_ptr() if C.numel() else 0, ld_of(C) if p.n > 0 else max(1, p.m)))
     tsmm_execute_grouped(items, _stream_handle(stream))
+
+
+def diag_bounded_wait(polls: int):
+    """Run the library's bounded mbarrier wait against a barrier that nothing
+    completes (tsmm_diag_bounded_wait); returns (status, cycles, seconds) --
+    status TIMEOUT (7) is the expected outcome."""
+    cyc = ctypes.c_uint64(0)
+    sec = ctypes.c_double(0.0)
+    st = lib.tsmm_diag_bounded_wait(int(polls), ctypes.byref(cyc), ctypes.byref(sec))
+    return int(st), int(cyc.value), float(sec.value)
 
 
 def autotune(A, pb: PackedB, C, reps: int = 5, stream=None) -> Plan:

@@ -9,11 +9,15 @@ namespace tsmm {
 // Device error record: kernels OR these bits into the plan's status word.
 enum : uint32_t { kDevErrTimeout = 1u };
 
-// Upper bound on polls of one mbarrier phase before a wait gives up.  Each poll
-// is an mbarrier.try_wait, which itself suspends the thread for a short,
-// hardware-defined interval, so the bound is generous (seconds) while
-// guaranteeing that a lost transaction can never hang the GPU.
+// A wait on an mbarrier phase gives up after kWaitNs of global time (one
+// second) or kMaxPolls polls, whichever comes first.  A poll is an
+// mbarrier.try_wait, which suspends the thread for a hardware-defined interval
+// while the phase is incomplete (about 3.8 us on GB300, measured), so the poll
+// cap alone would be about a minute; the clock makes the bound one second, far
+// above any legitimate wait (microseconds) and short enough that a lost
+// transaction costs the caller a TSMM_ERR_TIMEOUT, not a hung GPU.
 constexpr uint32_t kMaxPolls = 1u << 24;
+constexpr uint64_t kWaitNs = 1000000000ull;
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -55,11 +59,22 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
     return done != 0;
 }
 
-// Wait for the phase with the given parity to complete, polling at most
-// kMaxPolls times.  Returns false (and leaves the barrier alone) on timeout.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
-    for (uint32_t i = 0; i < kMaxPolls; ++i) {
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for the phase with the given parity to complete: at most max_polls
+// polls and kWaitNs of global time.  Returns false (and leaves the barrier
+// alone) on timeout.  The first poll is the fast path (no clock read).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity,
+                                                  uint32_t max_polls = kMaxPolls) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    for (uint32_t i = 1; i < max_polls; ++i) {
         if (mbar_try_wait(bar, parity)) return true;
+        if (global_ns() - t0 > kWaitNs) return false;
     }
     return false;
 }

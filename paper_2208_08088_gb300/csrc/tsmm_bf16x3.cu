@@ -378,17 +378,27 @@ __global__ void __launch_bounds__(320, 1)
         const int64_t slab = item / a.splits;
         const int split = (int)(item % a.splits);
         const int64_t i = slab * kBM + r;
-        auto store = [&](int jj, float v) {
-            if (i < a.m && jj < a.n) {
-                float o = (alpha == 1.f) ? v : alpha * v;
-                float *cp = C + i + (int64_t)jj * a.ldc;
-                if (beta != 0.f) o = fmaf(beta, *cp, o);
-                *cp = o;
+        // C = alpha*v + beta*C0 for columns c0 .. c0+15 of this thread's row: the
+        // 16 C0 loads are issued together, ahead of the stores
+        auto store16 = [&](int c0, const float *v) {
+            if (i >= a.m) return;
+            float *crow = C + i;
+            float c0v[16];
+#pragma unroll
+            for (int jj = 0; jj < 16; ++jj)
+                c0v[jj] = (beta != 0.f && c0 + jj < a.n) ? crow[(int64_t)(c0 + jj) * a.ldc] : 0.f;
+#pragma unroll
+            for (int jj = 0; jj < 16; ++jj) {
+                if (c0 + jj < a.n) {
+                    float o = (alpha == 1.f) ? v[jj] : alpha * v[jj];
+                    if (beta != 0.f) o = fmaf(beta, c0v[jj], o);
+                    crow[(int64_t)(c0 + jj) * a.ldc] = o;
+                }
             }
         };
         if (a.splits == 1) {
 #pragma unroll
-            for (int jj = 0; jj < NP; ++jj) store(jj, acc[jj]);
+            for (int c0 = 0; c0 < NP; c0 += 16) store16(c0, acc + c0);
             continue;
         }
 #pragma unroll
@@ -402,13 +412,34 @@ __global__ void __launch_bounds__(320, 1)
         named_barrier(3, 128);
         if (*flag == 0u) continue;
         __threadfence();
+        // last arriver: the S partials summed in the fixed order s = 0..S-1, 16
+        // columns at a time, the loads of split sp+1 in flight while split sp
+        // is added
+        const float *wrow = ws + slab * kBM + r;
 #pragma unroll
-        for (int jj = 0; jj < NP; ++jj) {
-            float sum = 0.f;
-            for (int sp = 0; sp < a.splits; ++sp)
-                sum += (sp == split) ? acc[jj]
-                                     : ld_cg(ws + ((int64_t)sp * NP + jj) * mpad + slab * kBM + r);
-            store(jj, sum);
+        for (int c0 = 0; c0 < NP; c0 += 16) {
+            float sum[16], t[16];
+#pragma unroll
+            for (int jj = 0; jj < 16; ++jj) {
+                sum[jj] = 0.f;
+                t[jj] = (split == 0) ? acc[c0 + jj] : ld_cg(wrow + (int64_t)(c0 + jj) * mpad);
+            }
+            for (int sp = 0; sp < a.splits; ++sp) {
+                float nt[16];
+                const int sn = sp + 1;
+                if (sn < a.splits) {
+#pragma unroll
+                    for (int jj = 0; jj < 16; ++jj)
+                        nt[jj] = (sn == split) ? acc[c0 + jj]
+                                               : ld_cg(wrow + ((int64_t)sn * NP + c0 + jj) * mpad);
+                }
+#pragma unroll
+                for (int jj = 0; jj < 16; ++jj) {
+                    sum[jj] += t[jj];
+                    t[jj] = nt[jj];
+                }
+            }
+            store16(c0, sum);
         }
         if (et == 0) a.tickets[slab] = 0u;
     }

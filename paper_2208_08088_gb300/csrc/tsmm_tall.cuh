@@ -131,19 +131,23 @@ __device__ __forceinline__ void tall_finish(T *red, const TallArgs &a, int64_t s
         named_barrier(1, Cfg::CONSUMERS);
     }
 
+    // C = alpha*v + beta*C0 for R rows of one column: the R C0 loads are
+    // issued together, ahead of the stores
     auto store = [&](int q, const Vec<T, R> &v) {
         const int j = (q * R) / Cfg::BM;
         const int il = (q * R) % Cfg::BM;
         if (j >= a.n) return;
-        T *cptr = static_cast<T *>(a.C);
+        T *c = static_cast<T *>(a.C) + row0 + il + (int64_t)j * a.ldc;
+        const int64_t rows = a.m - (row0 + il);  // rows of this chunk inside C
+        T c0[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) c0[r] = (beta != T(0) && r < rows) ? c[r] : T(0);
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            const int64_t i = row0 + il + r;
-            if (i < a.m) {
+            if (r < rows) {
                 T out = alpha * v.v[r];
-                T *c = cptr + i + (int64_t)j * a.ldc;
-                if (beta != T(0)) out = fma(beta, *c, out);
-                *c = out;
+                if (beta != T(0)) out = fma(beta, c0[r], out);
+                c[r] = out;
             }
         }
     };
@@ -175,10 +179,8 @@ __device__ __forceinline__ void tall_finish(T *red, const TallArgs &a, int64_t s
     for (int q = ctid; q < CHUNKS; q += Cfg::CONSUMERS) {
         const int j = (q * R) / Cfg::BM;
         const int il = (q * R) % Cfg::BM;
-        Vec<T, R> s;
-#pragma unroll
-        for (int r = 0; r < R; ++r) s.v[r] = T(0);
-        for (int sp = 0; sp < a.splits; ++sp) {
+        // partial of split sp (this block's own from shared memory)
+        auto partial = [&](int sp) {
             Vec<T, R> t;
             if (sp == split) {
                 t = ld_vec<T, R>(red + q * R);
@@ -187,8 +189,18 @@ __device__ __forceinline__ void tall_finish(T *red, const TallArgs &a, int64_t s
 #pragma unroll
                 for (int r = 0; r < R; ++r) t.v[r] = ld_cg(src + r);
             }
+            return t;
+        };
+        Vec<T, R> s;
+#pragma unroll
+        for (int r = 0; r < R; ++r) s.v[r] = T(0);
+        Vec<T, R> t = partial(0);
+        for (int sp = 0; sp < a.splits; ++sp) {
+            // the loads of split sp+1 are in flight while split sp is added
+            const Vec<T, R> nt = partial(sp + 1 < a.splits ? sp + 1 : sp);
 #pragma unroll
             for (int r = 0; r < R; ++r) s.v[r] += t.v[r];
+            t = nt;
         }
         store(q, s);
     }

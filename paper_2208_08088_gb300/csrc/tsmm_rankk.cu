@@ -144,10 +144,22 @@ struct RankEpilogue {
         }
     }
 
+    // alpha == 1 is a separate code path (the test is uniform), so the
+    // epilogue issues no multiply by 1 and no per-element select: at small k
+    // in FP64 the epilogue's arithmetic shares the FP64 pipe with the k
+    // products of each output.
     __device__ __forceinline__ void store(const RankAcc<T> &acc, const RankArgs &a, int64_t i0,
                                           int64_t tile, int tm, int tn, bool vec_c) const {
         const T alpha = static_cast<T>(a.alpha);
         const T beta = static_cast<T>(a.beta);
+        if (alpha == T(1)) store_t<true>(acc, a, i0, tile, tm, tn, vec_c, alpha, beta);
+        else store_t<false>(acc, a, i0, tile, tm, tn, vec_c, alpha, beta);
+    }
+
+    template <bool ALPHA1>
+    __device__ __forceinline__ void store_t(const RankAcc<T> &acc, const RankArgs &a, int64_t i0,
+                                            int64_t tile, int tm, int tn, bool vec_c, T alpha,
+                                            T beta) const {
         T *C = static_cast<T *>(a.C);
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
@@ -160,7 +172,7 @@ struct RankEpilogue {
 #pragma unroll
                 for (int r = 0; r < V; ++r) {
                     const T x = acc.get(rg * V + r, c);
-                    o.v[r] = (alpha == T(1)) ? x : alpha * x;  // alpha*x == x exactly when alpha is 1
+                    o.v[r] = ALPHA1 ? x : alpha * x;  // alpha*x == x exactly when alpha is 1
                     if (beta != T(0)) o.v[r] = fma(beta, c0v[c][rg].v[r], o.v[r]);
                 }
                 T *cp = C + i + j * a.ldc;

@@ -451,7 +451,8 @@ tsmm_status tsmm_execute(tsmm_plan_t p, double alpha, const void *A_dev, int64_t
         // box: bm rows x 32 columns (the regime (i) stage and the regime (ii) k chunk)
         const cuuint64_t gdim[2] = {(cuuint64_t)m, (cuuint64_t)k};
         const cuuint64_t gstride[1] = {(cuuint64_t)(lda * (int64_t)es)};
-        const cuuint32_t box[2] = {(cuuint32_t)p->bm, (cuuint32_t)kTallBKS};
+        const cuuint32_t box[2] = {(cuuint32_t)p->bm,
+                                   (cuuint32_t)a_box_k(p->dtype, p->regime, p->precision, p->k)};
         const cuuint32_t estr[2] = {1, 1};
         CUresult r = encoder()(&p->tmap,
                                p->dtype == TSMM_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
@@ -507,8 +508,9 @@ tsmm_status tsmm_execute(tsmm_plan_t p, double alpha, const void *A_dev, int64_t
         ra.alpha = alpha;
         ra.beta = beta;
         ra.num_sms = p->num_sms;
-        // C0 tile prefetch by TMA: needs the same 16-byte rules for C
-        const bool tmc = tma && beta != 0.0 && c_tma_ok(C_dev, ldc, n, es);
+        // C tiles by TMA (C0 prefetch; C0 and C in the FP32 k > 32 kernel): the
+        // same 16-byte rules for C
+        const bool tmc = tma && c_tma_ok(C_dev, ldc, n, es);
         if (tmc) {
             const tsmm_status st = encode_tmapc(p, C_dev, m, n, ldc, es, kRankNT);
             if (st != TSMM_OK) return st;

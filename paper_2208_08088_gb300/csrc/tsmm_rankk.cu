@@ -385,6 +385,321 @@ __global__ void __launch_bounds__(256, 2) rankk_plain_kernel(const RankArgs a, b
     ep.store(acc, a, i0, tile, tm, tn, vec_c);
 }
 
+// FP32, k > 32 (the FMA-bound shapes).  A 16-byte shared-memory load costs
+// four wavefronts whatever its address pattern, and the SM serves one per
+// cycle; the 8 x 4 register tiles above need 1.5 per cycle at the FMA peak,
+// so this kernel uses 8 x 8 tiles (1.0 per cycle): 4 consumer warps own the
+// same 128 x 64 C tile as a 2 x 2 grid of 64 x 32 warp tiles, lane
+// (lm = lane % 8, ln = lane / 8) owning rows {wm*64 + lm*4 + r, +32} and
+// columns {wn*32 + ln*4 + c, +16} (r, c < 4); a warp's A reads cover one
+// 128-byte line, its B reads 64 bytes.  To keep three blocks (12 consumer
+// warps) per SM in 227 KB, k streams in chunks of 16 through 3 stages
+// (12 KB each) and the C tile has one 32 KB buffer.
+//
+// TMA_EPI (C meets the TMA rules): the producer brings the C0 tile into the
+// buffer with one tensor copy while the tile's products run; the epilogue
+// overwrites it in place with alpha*acc + beta*C0, and one thread writes it
+// out with a TMA store and frees the buffer once the store has read it.
+// Otherwise the epilogue moves C0 and C with 16-byte loads and stores.
+namespace {
+template <bool TMA_EPI>
+struct WideCfg {
+    static constexpr int BMT = 128;
+    static constexpr int BNT = kRankNT;  // 64
+    static constexpr int KC = kRankWideKC;
+    static constexpr int STAGES = 3;
+    static constexpr int CONSUMERS = 128;
+    static constexpr int THREADS = CONSUMERS + 32;
+    static constexpr int A_CHUNK = BMT * KC;
+    static constexpr int B_CHUNK = KC * BNT;
+    static constexpr int STAGE_ELEMS = A_CHUNK + B_CHUNK;
+    static constexpr int C_ELEMS = TMA_EPI ? BMT * BNT : 0;  // [BNT][BMT], as the tensor copy lays it out
+    static constexpr int DATA_BYTES = (STAGES * STAGE_ELEMS + C_ELEMS) * 4;
+    static constexpr int NBAR = 2 * STAGES + 3;
+    static constexpr int SMEM = DATA_BYTES + NBAR * 8 + 16;
+    static_assert(3 * (SMEM + 1024) <= 228 * 1024, "three blocks per SM");
+};
+
+struct WideAcc {
+    float2 v[4][8];  // [row pair][column]
+    __device__ __forceinline__ void zero() {
+#pragma unroll
+        for (int rp = 0; rp < 4; ++rp)
+#pragma unroll
+            for (int c = 0; c < 8; ++c) v[rp][c] = make_float2(0.f, 0.f);
+    }
+    // row pairs rp: {r0 + 2rp, +1} for rp < 2, {r0 + 32 + 2(rp - 2), +1} after;
+    // columns c: c0 + c for c < 4, c0 + 16 + (c - 4) after
+    __device__ __forceinline__ void step(const float *As, const float *Bs, int pc, int r0, int c0) {
+        const float4 a0 = *reinterpret_cast<const float4 *>(As + pc * 128 + r0);
+        const float4 a1 = *reinterpret_cast<const float4 *>(As + pc * 128 + r0 + 32);
+        const float4 b0 = *reinterpret_cast<const float4 *>(Bs + pc * kRankNT + c0);
+        const float4 b1 = *reinterpret_cast<const float4 *>(Bs + pc * kRankNT + c0 + 16);
+        const float2 ap[4] = {make_float2(a0.x, a0.y), make_float2(a0.z, a0.w), make_float2(a1.x, a1.y),
+                              make_float2(a1.z, a1.w)};
+        const float bs[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const float2 bd = make_float2(bs[c], bs[c]);
+#pragma unroll
+            for (int rp = 0; rp < 4; ++rp) v[rp][c] = __ffma2_rn(ap[rp], bd, v[rp][c]);
+        }
+    }
+    // a full chunk is unrolled whole, so its loads can be scheduled early
+    template <int KC>
+    __device__ __forceinline__ void chunk(const float *As, const float *Bs, int kcnt, int r0, int c0) {
+        if (kcnt == KC) {
+#pragma unroll 8
+            for (int pc = 0; pc < KC; ++pc) step(As, Bs, pc, r0, c0);
+        } else {
+#pragma unroll 4
+            for (int pc = 0; pc < kcnt; ++pc) step(As, Bs, pc, r0, c0);
+        }
+    }
+    // the 4 rows of row group rg (0: r0.., 1: r0+32..) in column c (0..7)
+    __device__ __forceinline__ float4 rows(int rg, int c) const {
+        const float2 lo = v[rg * 2][c];
+        const float2 hi = v[rg * 2 + 1][c];
+        return make_float4(lo.x, lo.y, hi.x, hi.y);
+    }
+};
+
+__device__ __forceinline__ float4 axpby4(float alpha, float4 x, float beta, float4 c0, bool use_c0) {
+    x.x *= alpha;  // alpha*x == x exactly when alpha is 1
+    x.y *= alpha;
+    x.z *= alpha;
+    x.w *= alpha;
+    if (use_c0) {
+        x.x = fmaf(beta, c0.x, x.x);
+        x.y = fmaf(beta, c0.y, x.y);
+        x.z = fmaf(beta, c0.z, x.z);
+        x.w = fmaf(beta, c0.w, x.w);
+    }
+    return x;
+}
+
+__device__ __forceinline__ void tma_store_2d_commit(const void *tmap, const void *smem_src, int32_t x,
+                                                    int32_t y) {
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+                     reinterpret_cast<uint64_t>(tmap)),
+                 "r"(x), "r"(y), "r"(smem_addr(smem_src))
+                 : "memory");
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+}  // namespace
+
+template <bool TMA_EPI>
+__global__ void __launch_bounds__(WideCfg<TMA_EPI>::THREADS, 3)
+    rankk_wide_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmC,
+                      const RankArgs a, bool vec_c, unsigned *status) {
+    using W = WideCfg<TMA_EPI>;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    float *sStage = reinterpret_cast<float *>(smem_raw);
+    float *cbuf = sStage + W::STAGES * W::STAGE_ELEMS;
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem_raw + W::DATA_BYTES);
+    uint64_t *empty = full + W::STAGES;
+    uint64_t *cfull = empty + W::STAGES;  // C0 landed (or buffer free, beta == 0)
+    uint64_t *cstore = cfull + 1;         // results written (4 consumer warps)
+    uint64_t *cempty = cstore + 1;        // the store has read the buffer
+
+    const int warp = threadIdx.x / 32;
+    const int lane = threadIdx.x % 32;
+    const int64_t mtiles = (a.m + W::BMT - 1) / W::BMT;
+    const int64_t ntiles_total = mtiles * ((a.n + W::BNT - 1) / W::BNT);
+    const int nchunks = (int)((a.k + W::KC - 1) / W::KC);
+    const bool use_c0 = a.beta != 0.0;
+
+    if (threadIdx.x == 0) {
+        prefetch_tmap(&tmA);
+        if (TMA_EPI) prefetch_tmap(&tmC);
+        for (int s = 0; s < W::STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], W::CONSUMERS / 32);
+        }
+        mbar_init(cfull, 1);
+        mbar_init(cstore, W::CONSUMERS / 32);
+        mbar_init(cempty, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    if (warp == W::CONSUMERS / 32) {
+        // ------------------------------------------------ producer
+        if (lane == 0) {
+            const uint64_t pol_keep = policy_evict_last();
+            const uint64_t pol_stream = policy_evict_first();
+            int64_t g = 0;
+            int j = 0;
+            bool ok = true;
+            for (int64_t t = blockIdx.x; t < ntiles_total && ok; t += gridDim.x, ++j) {
+                const int64_t i0 = (t % mtiles) * W::BMT;
+                const int64_t tile = t / mtiles;
+                const float *Bt = static_cast<const float *>(a.Bp) + tile * a.kp * W::BNT;
+                for (int c = 0; c < nchunks; ++c, ++g) {
+                    const int st = (int)(g % W::STAGES);
+                    if (g >= W::STAGES &&
+                        !mbar_wait_bounded(&empty[st], (uint32_t)((g / W::STAGES) & 1) ^ 1)) {
+                        ok = false;
+                        break;
+                    }
+                    const int64_t kc = (int64_t)c * W::KC;
+                    const int brows = (int)((a.kp - kc < W::KC) ? a.kp - kc : W::KC);
+                    float *sA = sStage + st * W::STAGE_ELEMS;
+                    mbar_arrive_expect_tx(&full[st], (W::A_CHUNK + brows * W::BNT) * 4);
+                    tma_load_2d(sA, &tmA, (int32_t)i0, (int32_t)kc, &full[st], pol_keep);
+                    bulk_load(sA + W::A_CHUNK, Bt + kc * W::BNT, brows * W::BNT * 4, &full[st], pol_keep);
+                    // the C0 tile follows the tile's second chunk (k > 32: there always is
+                    // one), so two chunks are in flight while the previous tile's store drains
+                    if (TMA_EPI && c == 1) {
+                        if (j >= 1 && !mbar_wait_bounded(cempty, (uint32_t)((j - 1) & 1))) {
+                            ok = false;
+                            break;
+                        }
+                        if (use_c0) {
+                            mbar_arrive_expect_tx(cfull, W::C_ELEMS * 4);
+                            tma_load_2d(cbuf, &tmC, (int32_t)i0, (int32_t)(tile * W::BNT), cfull, pol_stream);
+                        } else {
+                            mbar_arrive(cfull);
+                        }
+                    }
+                }
+            }
+            if (!ok) atomicOr(status, kDevErrTimeout);
+            // copies in flight land before the block may exit
+            for (int64_t q = g > W::STAGES ? g - W::STAGES : 0; q < g; ++q)
+                mbar_wait_bounded(&full[q % W::STAGES], (uint32_t)((q / W::STAGES) & 1));
+            if (TMA_EPI && j >= 1) mbar_wait_bounded(cfull, (uint32_t)((j - 1) & 1));
+        }
+        return;
+    }
+
+    // ---------------------------------------------------- consumers
+    const int lm = lane & 7;
+    const int ln = lane >> 3;
+    const int r0 = (warp & 1) * 64 + lm * 4;   // local rows r0..r0+3 and r0+32..r0+35
+    const int c0 = (warp >> 1) * 32 + ln * 4;  // local columns c0..c0+3 and c0+16..c0+19
+    const float alpha = static_cast<float>(a.alpha);
+    const float beta = static_cast<float>(a.beta);
+    float *C = static_cast<float *>(a.C);
+    int64_t g = 0;
+    int j = 0;
+    bool ok = true;
+    for (int64_t t = blockIdx.x; t < ntiles_total && ok; t += gridDim.x, ++j) {
+        const int64_t i0 = (t % mtiles) * W::BMT;
+        const int64_t tile = t / mtiles;
+        WideAcc acc;
+        acc.zero();
+        for (int c = 0; c < nchunks; ++c, ++g) {
+            const int st = (int)(g % W::STAGES);
+            if (!mbar_wait_bounded(&full[st], (uint32_t)((g / W::STAGES) & 1))) {
+                ok = false;
+                break;
+            }
+            const int64_t kc = (int64_t)c * W::KC;
+            const int kcnt = (int)((a.k - kc < W::KC) ? a.k - kc : W::KC);
+            const float *sA = sStage + st * W::STAGE_ELEMS;
+            acc.chunk<W::KC>(sA, sA + W::A_CHUNK, kcnt, r0, c0);
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[st]);
+        }
+        if (!ok) break;
+        if (TMA_EPI) {
+            if (!__all_sync(0xffffffffu, mbar_wait_bounded(cfull, (uint32_t)(j & 1)))) {
+                ok = false;
+                break;
+            }
+#pragma unroll
+            for (int cc = 0; cc < 8; ++cc) {
+                const int cl = c0 + (cc < 4 ? cc : 12 + cc);
+#pragma unroll
+                for (int rg = 0; rg < 2; ++rg) {
+                    float4 *p = reinterpret_cast<float4 *>(cbuf + cl * W::BMT + r0 + rg * 32);
+                    const float4 c0v = use_c0 ? *p : make_float4(0.f, 0.f, 0.f, 0.f);
+                    *p = axpby4(alpha, acc.rows(rg, cc), beta, c0v, use_c0);
+                }
+            }
+            fence_proxy_async_smem();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(cstore);
+            if (threadIdx.x == 0) {
+                // every warp's results are in: write the tile, free the buffer
+                if (!mbar_wait_bounded(cstore, (uint32_t)(j & 1))) {
+                    ok = false;
+                } else {
+                    tma_store_2d_commit(&tmC, cbuf, (int32_t)i0, (int32_t)(tile * W::BNT));
+                    asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+                    mbar_arrive(cempty);
+                }
+            }
+            continue;
+        }
+        // plain epilogue in two halves of 4 columns: all C0 loads of a half before its stores
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            float4 c0v[4][2];
+#pragma unroll
+            for (int cc = 0; cc < 4; ++cc) {
+                const int64_t jg = tile * W::BNT + c0 + h * 16 + cc;
+#pragma unroll
+                for (int rg = 0; rg < 2; ++rg) {
+                    const int64_t i = i0 + r0 + rg * 32;
+                    c0v[cc][rg] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (!use_c0 || jg >= a.n) continue;
+                    const float *src = C + i + jg * a.ldc;
+                    if (vec_c && i + 4 <= a.m) {
+                        c0v[cc][rg] = *reinterpret_cast<const float4 *>(src);
+                    } else {
+                        if (i < a.m) c0v[cc][rg].x = src[0];
+                        if (i + 1 < a.m) c0v[cc][rg].y = src[1];
+                        if (i + 2 < a.m) c0v[cc][rg].z = src[2];
+                        if (i + 3 < a.m) c0v[cc][rg].w = src[3];
+                    }
+                }
+            }
+#pragma unroll
+            for (int cc = 0; cc < 4; ++cc) {
+                const int64_t jg = tile * W::BNT + c0 + h * 16 + cc;
+                if (jg >= a.n) continue;
+#pragma unroll
+                for (int rg = 0; rg < 2; ++rg) {
+                    const int64_t i = i0 + r0 + rg * 32;
+                    const float4 x = acc.rows(rg, h * 4 + cc);
+                    const float4 o = axpby4(alpha, x, beta, c0v[cc][rg], use_c0);
+                    float *dst = C + i + jg * a.ldc;
+                    if (vec_c && i + 4 <= a.m) {
+                        *reinterpret_cast<float4 *>(dst) = o;
+                    } else {
+                        if (i < a.m) dst[0] = o.x;
+                        if (i + 1 < a.m) dst[1] = o.y;
+                        if (i + 2 < a.m) dst[2] = o.z;
+                        if (i + 3 < a.m) dst[3] = o.w;
+                    }
+                }
+            }
+        }
+    }
+    if (!ok && lane == 0) atomicOr(status, kDevErrTimeout);
+    if (TMA_EPI && threadIdx.x == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+}
+
+template <bool TMA_EPI>
+static cudaError_t launch_rankk_wide_t(const CUtensorMap *tmA, const CUtensorMap *tmC, const RankArgs &a,
+                                       bool vec_c, unsigned *status, cudaStream_t s) {
+    using W = WideCfg<TMA_EPI>;
+    static bool attr_done = false;
+    if (!attr_done) {
+        cudaError_t e = cudaFuncSetAttribute(rankk_wide_kernel<TMA_EPI>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, W::SMEM);
+        if (e != cudaSuccess) return e;
+        attr_done = true;
+    }
+    const int64_t tiles = ((a.m + W::BMT - 1) / W::BMT) * ((a.n + W::BNT - 1) / W::BNT);
+    const int64_t slots = 3 * (int64_t)(a.num_sms > 0 ? a.num_sms : 1);
+    const unsigned grid = (unsigned)(tiles < slots ? tiles : slots);
+    rankk_wide_kernel<TMA_EPI><<<grid, W::THREADS, W::SMEM, s>>>(*tmA, *tmC, a, vec_c, status);
+    return cudaGetLastError();
+}
+
 template <typename T, int STAGES, bool PF>
 static cudaError_t launch_rankk_tma_t(const CUtensorMap *tmA, const CUtensorMap *tmC,
                                       const RankArgs &a, bool vec_c, unsigned *status,
@@ -419,6 +734,10 @@ static cudaError_t launch_rankk_t(const CUtensorMap *tmA, const CUtensorMap *tmC
             if (tmC && a.beta != 0.0) return launch_rankk_tma_t<T, 1, true>(tmA, tmC, a, vec_c, status, s);
             return launch_rankk_tma_t<T, 1, false>(tmA, tmA, a, vec_c, status, s);
         }
+        // FP32, k > 32: the 8 x 8-tile kernel (its A tensor map has a 128 x 16 box)
+        if (sizeof(T) == 4)
+            return tmC ? launch_rankk_wide_t<true>(tmA, tmC, a, vec_c, status, s)
+                       : launch_rankk_wide_t<false>(tmA, tmA, a, vec_c, status, s);
         return launch_rankk_tma_t<T, 2, false>(tmA, tmA, a, vec_c, status, s);
     }
     const int smem = Cfg::KC * (Cfg::BMT + Cfg::BNT) * (int)sizeof(T);

@@ -348,10 +348,20 @@ def run_ours(args):
         if (m, k) not in A:
             A[(m, k)] = dmat(m, k, ti.SEED_A)
     packed, plans, C = {}, {}, {}
+    pack_ms = {}  # tsmm_pack_b time per B (once per B, outside the timed steps)
     prec = tsmm.PREC_BF16X3 if args.precision == "bf16x3" else tsmm.PREC_NATIVE
     for (m, n, k, beta) in pts:
         if (n, k) not in packed:
-            packed[(n, k)] = tsmm.pack_b(dmat(k, n, ti.SEED_B), precision=prec)
+            Bsrc = dmat(k, n, ti.SEED_B)
+            tsmm.pack_b(Bsrc, precision=prec)  # first call: kernel attributes, module load
+            p0 = torch.cuda.Event(enable_timing=True)
+            p1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            p0.record(stream)
+            packed[(n, k)] = tsmm.pack_b(Bsrc, precision=prec)
+            p1.record(stream)
+            torch.cuda.synchronize()
+            pack_ms[f"n={n},k={k}"] = round(p0.elapsed_time(p1), 4)
             plans[(m, n, k)] = tsmm.plan(m, n, k, tdt, precision=prec)
             C[(m, n)] = dmat(m, n, ti.SEED_C0)  # C0; beta = 1 updates it in place
     torch.cuda.synchronize()
@@ -461,7 +471,7 @@ def run_ours(args):
                                          "larger than the 129 MB L2",
                    "parallelism": f"replicas x{world} (independent problems per GPU)"},
         "clocks": clocks, "gpu_launches": launches, "e2e": e2e, "roofline": roof,
-        "points": points,
+        "points": points, "pack_ms": pack_ms,
     }
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = oracle_sample(args, A)
@@ -573,10 +583,13 @@ def run_precision(args):
     k in {64, 128}; A and B entries N(0,1) * 10**U[-3,3] per row, alpha = 1,
     beta = 0.  Each shape is computed in FP32 (IEEE FMA), in the BF16x3
     tensor-core mode and in FP64 (FMA) on the same inputs; the JSON line gives
-    each launch's time and its error against the FP64 oracle on 32 sampled rows."""
+    each launch's time and its error on 32 sampled rows against the exactly
+    rounded result: the inputs are FP32 values, so every product is exact in
+    FP64, and math.fsum returns the correctly rounded sum of the k products."""
+    import math
+
     import torch
 
-    import oracle
     import paper_2208_08088_gb300 as tsmm
     import tsmm_inputs as ti
 
@@ -595,7 +608,10 @@ def run_precision(args):
         rows = np.sort(np.random.default_rng(7).choice(m, 32, replace=False))
         A_rows = np.asfortranarray(A32[torch.as_tensor(rows, device="cuda")].cpu().numpy().astype(np.float64))
         B_host = np.asfortranarray(B32.cpu().numpy().astype(np.float64))
-        Cref, _ = oracle.tsmm(1.0, A_rows, B_host, 0.0, None)
+        Cref = np.empty((len(rows), n))
+        for ri in range(len(rows)):
+            P = A_rows[ri][:, None] * B_host  # k x n exact products
+            Cref[ri] = [math.fsum(P[:, j]) for j in range(n)]
         G = np.abs(A_rows) @ np.abs(B_host)
         for name, dt, prec in (("fp32_fma", torch.float32, tsmm.PREC_NATIVE),
                                ("bf16x3_tcgen05", torch.float32, tsmm.PREC_BF16X3),
@@ -638,7 +654,8 @@ def run_precision(args):
             "config": {"workload": "precision mode: m=k=32768 n=64, and m=n=16384 k in {64,128}; "
                                    "A and B entries N(0,1)*10^U[-3,3] per row, alpha=1, beta=0; "
                                    "value = BF16x3 GFLOP/s over the three shapes",
-                       "error_reference": "FP64 oracle (compensated Dot2) on 32 sampled rows"},
+                       "error_reference": "exactly rounded sums of the exact FP64 products "
+                                          "(math.fsum) on 32 sampled rows"},
             "modes": out}
     print(json.dumps(line))
     return 0

@@ -584,6 +584,7 @@ __global__ void __launch_bounds__(WideCfg<TMA_EPI>::THREADS, 3)
     int64_t g = 0;
     int j = 0;
     bool ok = true;
+    bool release_pending = false;  // thread 0: a store whose buffer is not yet freed
     for (int64_t t = blockIdx.x; t < ntiles_total && ok; t += gridDim.x, ++j) {
         const int64_t i0 = (t % mtiles) * W::BMT;
         const int64_t tile = t / mtiles;
@@ -601,6 +602,14 @@ __global__ void __launch_bounds__(WideCfg<TMA_EPI>::THREADS, 3)
             acc.chunk<W::KC>(sA, sA + W::A_CHUNK, kcnt, r0, c0);
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty[st]);
+            if (TMA_EPI && release_pending) {
+                // one chunk after the previous tile's store was issued it has read
+                // the buffer long since: free it for the next C0 (the producer
+                // asks for it after this tile's second chunk)
+                asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+                mbar_arrive(cempty);
+                release_pending = false;
+            }
         }
         if (!ok) break;
         if (TMA_EPI) {
@@ -622,13 +631,13 @@ __global__ void __launch_bounds__(WideCfg<TMA_EPI>::THREADS, 3)
             __syncwarp();
             if (lane == 0) mbar_arrive(cstore);
             if (threadIdx.x == 0) {
-                // every warp's results are in: write the tile, free the buffer
+                // every warp's results are in: write the tile; the buffer is freed
+                // after this thread's next chunk
                 if (!mbar_wait_bounded(cstore, (uint32_t)(j & 1))) {
                     ok = false;
                 } else {
                     tma_store_2d_commit(&tmC, cbuf, (int32_t)i0, (int32_t)(tile * W::BNT));
-                    asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
-                    mbar_arrive(cempty);
+                    release_pending = true;
                 }
             }
             continue;

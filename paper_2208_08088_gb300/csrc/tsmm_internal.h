@@ -122,12 +122,15 @@ struct RankArgs {
     int num_sms;     // persistent grid size = resident blocks x SMs
 };
 // tmA: tensor map of A (box bm x 32) or nullptr for the plain-load kernel;
-// k chunk of the FP32 regime (ii) kernel for k > kRankKC32 (its A tensor map box is bm x kRankWideKC;
-// every other kernel's is bm x kTallBKS).
+// The FP32 regime (ii) kernel for k > kRankWideMinK - 1 streams k in chunks of kRankWideKC (its A
+// tensor map box is bm x kRankWideKC; every other kernel's is bm x kTallBKS).
 constexpr int kRankWideKC = 16;
-constexpr int kRankKC32 = 32;
+constexpr int kRankWideMinK = kRankWideKC + 1;  // at least two chunks
+inline bool rank_wide(tsmm_dtype d, int regime, int precision, int64_t k) {
+    return d == TSMM_F32 && regime == 2 && precision == 0 && k >= kRankWideMinK;
+}
 inline int a_box_k(tsmm_dtype d, int regime, int precision, int64_t k) {
-    return (d == TSMM_F32 && regime == 2 && precision == 0 && k > kRankKC32) ? kRankWideKC : kTallBKS;
+    return rank_wide(d, regime, precision, k) ? kRankWideKC : kTallBKS;
 }
 // tmC: tensor map of C (box bm x kRankNT) when C meets the TMA rules, else nullptr.
 cudaError_t launch_rankk(tsmm_dtype dt, const CUtensorMap *tmA, const CUtensorMap *tmC,

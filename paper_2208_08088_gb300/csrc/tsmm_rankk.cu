@@ -385,7 +385,7 @@ __global__ void __launch_bounds__(256, 2) rankk_plain_kernel(const RankArgs a, b
     ep.store(acc, a, i0, tile, tm, tn, vec_c);
 }
 
-// FP32, k > 32 (the FMA-bound shapes).  A 16-byte shared-memory load costs
+// FP32, k > 16 (FMA-bound, or near the ridge).  A 16-byte shared-memory load costs
 // four wavefronts whatever its address pattern, and the SM serves one per
 // cycle; the 8 x 4 register tiles above need 1.5 per cycle at the FMA peak,
 // so this kernel uses 8 x 8 tiles (1.0 per cycle): 4 consumer warps own the
@@ -548,8 +548,9 @@ __global__ void __launch_bounds__(WideCfg<TMA_EPI>::THREADS, 3)
                     mbar_arrive_expect_tx(&full[st], (W::A_CHUNK + brows * W::BNT) * 4);
                     tma_load_2d(sA, &tmA, (int32_t)i0, (int32_t)kc, &full[st], pol_keep);
                     bulk_load(sA + W::A_CHUNK, Bt + kc * W::BNT, brows * W::BNT * 4, &full[st], pol_keep);
-                    // the C0 tile follows the tile's second chunk (k > 32: there always is
-                    // one), so two chunks are in flight while the previous tile's store drains
+                    // the C0 tile follows the tile's second chunk (k >= kRankWideMinK: there
+                    // always is one), so two chunks are in flight while the previous
+                    // tile's store drains
                     if (TMA_EPI && c == 1) {
                         if (j >= 1 && !mbar_wait_bounded(cempty, (uint32_t)((j - 1) & 1))) {
                             ok = false;
@@ -738,15 +739,15 @@ static cudaError_t launch_rankk_t(const CUtensorMap *tmA, const CUtensorMap *tmC
     const bool vec_c = (reinterpret_cast<uintptr_t>(a.C) % 16 == 0) &&
                        ((a.ldc * (int64_t)sizeof(T)) % 16 == 0);
     if (tmA) {
+        // FP32 from k = kRankWideMinK on: the 8 x 8-tile kernel (its A tensor map has a 128 x 16 box)
+        if (rank_wide(sizeof(T) == 4 ? TSMM_F32 : TSMM_F64, 2, 0, a.k))
+            return tmC ? launch_rankk_wide_t<true>(tmA, tmC, a, vec_c, status, s)
+                       : launch_rankk_wide_t<false>(tmA, tmA, a, vec_c, status, s);
         // output-bound shapes: one k chunk, C0 prefetched by TMA when it is read
         if (a.k <= Cfg::KC) {
             if (tmC && a.beta != 0.0) return launch_rankk_tma_t<T, 1, true>(tmA, tmC, a, vec_c, status, s);
             return launch_rankk_tma_t<T, 1, false>(tmA, tmA, a, vec_c, status, s);
         }
-        // FP32, k > 32: the 8 x 8-tile kernel (its A tensor map has a 128 x 16 box)
-        if (sizeof(T) == 4)
-            return tmC ? launch_rankk_wide_t<true>(tmA, tmC, a, vec_c, status, s)
-                       : launch_rankk_wide_t<false>(tmA, tmA, a, vec_c, status, s);
         return launch_rankk_tma_t<T, 2, false>(tmA, tmA, a, vec_c, status, s);
     }
     const int smem = Cfg::KC * (Cfg::BMT + Cfg::BNT) * (int)sizeof(T);

@@ -181,7 +181,7 @@ def test_ieee_specials_propagate(dtype):
 
 # ------------------------------------------------------------- regime (ii)
 @pytest.mark.parametrize("dtype", DT)
-@pytest.mark.parametrize("k", [1, 4, 7, 32, 37, 64, 128])
+@pytest.mark.parametrize("k", [1, 4, 7, 16, 17, 32, 37, 48, 64, 127, 128])
 def test_rankk_ragged(dtype, k):
     m, n = 1000, 300
     A, B, C0 = gen(m, n, k, dtype)

@@ -117,7 +117,8 @@ TSMM_API const char *tsmm_last_cuda_error(void);
  *
  * Packed layout (private to the library, described for test readers): the
  * n columns are cut into `ntiles` tiles of `w` columns (regime (i): one tile,
- * w = the kernel's padded column count; regime (ii): w = 64).  Tile t is a
+ * w = the kernel's padded column count, n rounded up to one of 1, 2, 4, 8, 16,
+ * 24, 32, 48, 64; regime (ii): w = 64).  Tile t is a
  * row-major kp x w block (kp = k rounded up to the kernel's k granule) at
  * element offset t*kp*w; element (p, jj) of tile t holds B[p, t*w + jj], and is
  * +0.0 where p >= k or t*w + jj >= n.
@@ -364,7 +365,7 @@ TSMM_API double tsmm_server_clock(void);
  * device array of TSMM_NOALLOC_SCRATCH_BYTES (32 MiB) that every GPU loading
  * the library holds until the process exits.  The k split is reduced so the
  * partial tiles fit; sizes whose packed B (k rounded up to 32, times n rounded
- * up to a power of two, times the element size) plus one arrival counter per
+ * up to one of 1, 2, 4, 8, 16, 24, 32, 48, 64, times the element size) plus one arrival counter per
  * 128 (F32) / 64 (F64) rows of m do not fit return TSMM_ERR_UNSUPPORTED_SHAPE
  * before any device work, as do shapes with n > 64.
  *

@@ -190,7 +190,9 @@ cudaError_t launch_grouped_dispatch(int np, const GroupParams &gp, int num_sms, 
         case 4: return launch_grouped_t<T, 4>(gp, num_sms, s);
         case 8: return launch_grouped_t<T, 8>(gp, num_sms, s);
         case 16: return launch_grouped_t<T, 16>(gp, num_sms, s);
+        case 24: return launch_grouped_t<T, 24>(gp, num_sms, s);
         case 32: return launch_grouped_t<T, 32>(gp, num_sms, s);
+        case 48: return launch_grouped_t<T, 48>(gp, num_sms, s);
         case 64: return launch_grouped_t<T, 64>(gp, num_sms, s);
         default: return cudaErrorInvalidValue;
     }

@@ -23,11 +23,20 @@ constexpr int kTallMaxN = 64;
 
 inline size_t dtype_size(tsmm_dtype d) { return d == TSMM_F64 ? 8 : 4; }
 
-// Padded column count of the regime-(i) kernel that serves n columns.
-inline int tall_np(int64_t n) {
+// Smallest power of two >= n.
+inline int pow2_ceil(int64_t n) {
     int np = 1;
     while (np < n) np <<= 1;
     return np;
+}
+
+// Padded column count of the regime-(i) kernel that serves n columns: one of
+// 1, 2, 4, 8, 16, 24, 32, 48, 64 (the FMA-bound widths 24 and 48 save a
+// quarter of the padded work for n in 17..24 and 33..48).
+inline int tall_np(int64_t n) {
+    if (n > 16 && n <= 24) return 24;
+    if (n > 32 && n <= 48) return 48;
+    return pow2_ceil(n);
 }
 
 // Rows per thread block of the regime-(i) kernel (see tall kernel header).
@@ -150,7 +159,7 @@ tsmm_status plan_layout(int64_t m, int64_t n, int64_t k, tsmm_dtype dtype, int f
 // BF16x3 precision mode (tsmm_bf16x3.cu): k granule of its packed B and plan.
 constexpr int kX3KB = 64;
 inline int x3_np(int64_t n) {
-    const int np = tall_np(n);
+    const int np = pow2_ceil(n);  // an MMA N of 16, 32 or 64
     return np < 16 ? 16 : np;
 }
 cudaError_t launch_tall_bf16x3(int np, const CUtensorMap *tmap, const TallArgs &a, int num_sms,

@@ -39,9 +39,10 @@ struct TallCfg {
     // tile's 5 loads per 32 fmas saturate them before the FMA pipe).  A
     // thread's 8 rows are two groups of 4, half a warp tile apart, so the
     // lanes along m read adjacent 16-byte words of A (no bank shared).
-    static constexpr bool WIDE = sizeof(T) == 4 && NP >= 32;
-    static constexpr int R = WIDE ? 8 : VEC;                  // rows per thread
-    static constexpr int CN = WIDE ? 8 : (NP < 16 ? NP : 16);  // columns per thread
+    // The widths 24 and 48 use 12 columns per thread (2 or 4 lane groups).
+    static constexpr bool WIDE = sizeof(T) == 4 && (NP == 32 || NP == 64);
+    static constexpr int R = WIDE ? 8 : VEC;  // rows per thread
+    static constexpr int CN = WIDE ? 8 : ((NP == 24 || NP == 48) ? 12 : (NP < 16 ? NP : 16));  // columns per thread
     static constexpr int G = NP / CN;                  // lane groups along n
     static constexpr int LR = 32 / G;                  // lanes along m
     static constexpr int WROWS = LR * R;               // rows per warp
@@ -481,7 +482,9 @@ cudaError_t launch_tall_dispatch(bool tma, int np, const CUtensorMap *tmap, cons
         TSMM_TALL_CASE(4)
         TSMM_TALL_CASE(8)
         TSMM_TALL_CASE(16)
+        TSMM_TALL_CASE(24)
         TSMM_TALL_CASE(32)
+        TSMM_TALL_CASE(48)
         TSMM_TALL_CASE(64)
         default:
             return cudaErrorInvalidValue;

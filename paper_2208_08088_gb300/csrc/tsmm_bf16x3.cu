@@ -203,8 +203,9 @@ __global__ void __launch_bounds__(320, 1)
             int64_t g = 0;
             bool ok = true;
             for (int64_t item = blockIdx.x; item < total && ok; item += gridDim.x) {
-                const int64_t slab = item / a.splits;
-                const int64_t k0 = (item % a.splits) * a.kchunk;
+                int64_t slab, sp;
+                udivmod(item, a.splits, slab, sp);
+                const int64_t k0 = sp * a.kchunk;
                 const int64_t k1 = (k0 + a.kchunk < a.kp) ? k0 + a.kchunk : a.kp;
                 for (int64_t kk = k0; kk < k1; kk += kKB, ++g) {
                     const int s = (int)(g % kS);
@@ -241,7 +242,9 @@ __global__ void __launch_bounds__(320, 1)
                 }
                 tc_fence_after();
                 const uint32_t tacc = tmem + (uint32_t)(b * NP);
-                const int64_t k0 = (item % a.splits) * a.kchunk;
+                int64_t slab_, sp;
+                udivmod(item, a.splits, slab_, sp);
+                const int64_t k0 = sp * a.kchunk;
                 const int64_t k1 = (k0 + a.kchunk < a.kp) ? k0 + a.kchunk : a.kp;
                 bool first = true;
                 for (int64_t kk = k0; kk < k1; kk += kKB, ++g) {
@@ -290,7 +293,9 @@ __global__ void __launch_bounds__(320, 1)
         int64_t g = 0;
         bool ok = true;
         for (int64_t item = blockIdx.x; item < total && ok; item += gridDim.x) {
-            const int64_t k0 = (item % a.splits) * a.kchunk;
+            int64_t slab_, sp;
+            udivmod(item, a.splits, slab_, sp);
+            const int64_t k0 = sp * a.kchunk;
             const int64_t k1 = (k0 + a.kchunk < a.kp) ? k0 + a.kchunk : a.kp;
             for (int64_t kk = k0; kk < k1; kk += kKB, ++g) {
                 const int s = (int)(g % kS);
@@ -375,8 +380,9 @@ __global__ void __launch_bounds__(320, 1)
         __syncwarp();
         if (lane == 0) mbar_arrive(&tempty[b]);  // the MMAs may reuse this accumulator
 
-        const int64_t slab = item / a.splits;
-        const int split = (int)(item % a.splits);
+        int64_t slab, sp64;
+        udivmod(item, a.splits, slab, sp64);
+        const int split = (int)sp64;
         const int64_t i = slab * kBM + r;
         // C = alpha*v + beta*C0 for columns c0 .. c0+15 of this thread's row: the
         // 16 C0 loads are issued together, ahead of the stores
@@ -687,8 +693,9 @@ __global__ void __launch_bounds__(512, 1)
             int j = 0;
             bool ok = true;
             for (int64_t item = blockIdx.x; item < total && ok; item += gridDim.x, ++j) {
-                const int64_t mt = item / nch;
-                const int64_t t0 = (item % nch) * rnch;
+                int64_t mt, ch;
+                udivmod(item, nch, mt, ch);
+                const int64_t t0 = ch * rnch;
                 const int64_t t1 = (t0 + rnch < ntiles) ? t0 + rnch : ntiles;
                 if (j >= 1 && !mbar_wait_bounded(a_empty, (uint32_t)((j - 1) & 1))) {
                     ok = false;
@@ -728,8 +735,9 @@ __global__ void __launch_bounds__(512, 1)
         int64_t q = 0;  // sub-tiles issued
         bool ok = true;
         for (int64_t item = blockIdx.x; item < total && ok; item += gridDim.x) {
-            const int64_t mt = item / nch;
-            const int64_t t0 = (item % nch) * rnch;
+            int64_t mt, ch;
+            udivmod(item, nch, mt, ch);
+            const int64_t t0 = ch * rnch;
             const int64_t t1 = (t0 + rnch < ntiles) ? t0 + rnch : ntiles;
             for (int64_t t = t0; t < t1 && ok; ++t) {
                 for (int sub = 0; sub < kRSUBS; ++sub, ++q) {
@@ -772,8 +780,9 @@ __global__ void __launch_bounds__(512, 1)
         int64_t q = 0;  // sub-tiles stored
         bool ok = true;
         for (int64_t item = blockIdx.x; item < total && ok; item += gridDim.x) {
-            const int64_t mt = item / nch;
-            const int64_t t0 = (item % nch) * rnch;
+            int64_t mt, ch;
+            udivmod(item, nch, mt, ch);
+            const int64_t t0 = ch * rnch;
             const int64_t t1 = (t0 + rnch < ntiles) ? t0 + rnch : ntiles;
             for (int64_t t = t0; t < t1 && ok; ++t) {
                 for (int sub = 0; sub < kRSUBS; ++sub, ++q) {
@@ -809,7 +818,9 @@ __global__ void __launch_bounds__(512, 1)
             int j = 0;
             bool ok = true;
             for (int64_t item = blockIdx.x; item < total && ok; item += gridDim.x, ++j) {
-                const int64_t t0 = (item % nch) * rnch;
+                int64_t mt_, ch;
+                udivmod(item, nch, mt_, ch);
+                const int64_t t0 = ch * rnch;
                 const int64_t t1 = (t0 + rnch < ntiles) ? t0 + rnch : ntiles;
                 if (!mbar_wait_bounded(a_conv, (uint32_t)(j & 1))) {
                     ok = false;
@@ -921,8 +932,9 @@ __global__ void __launch_bounds__(512, 1)
     int64_t g = 0, gc = 0;
     bool ok = true;
     for (int64_t item = blockIdx.x; item < total && ok; item += gridDim.x) {
-        const int64_t mt = item / nch;
-        const int64_t t0 = (item % nch) * rnch;
+        int64_t mt, ch;
+        udivmod(item, nch, mt, ch);
+        const int64_t t0 = ch * rnch;
         const int64_t t1 = (t0 + rnch < ntiles) ? t0 + rnch : ntiles;
         const int64_t i = mt * kBM + quarter * 32 + lane;
         float *crow = C + i;

@@ -19,6 +19,20 @@ enum : uint32_t { kDevErrTimeout = 1u };
 constexpr uint32_t kMaxPolls = 1u << 24;
 constexpr uint64_t kWaitNs = 1000000000ull;
 
+// Quotient and remainder of a / b for 0 <= a, 0 < b.  A 64-bit division is a
+// long sequence that occupies the (slow) FP64 pipe on this GPU; per-tile index
+// math takes the 32-bit path whenever both operands fit.
+__device__ __forceinline__ void udivmod(int64_t a, int64_t b, int64_t &q, int64_t &r) {
+    if (((static_cast<uint64_t>(a) | static_cast<uint64_t>(b)) >> 32) == 0) {
+        const uint32_t q32 = static_cast<uint32_t>(a) / static_cast<uint32_t>(b);
+        q = q32;
+        r = static_cast<int64_t>(static_cast<uint32_t>(a) - q32 * static_cast<uint32_t>(b));
+    } else {
+        q = a / b;
+        r = a - q * b;
+    }
+}
+
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }

@@ -86,8 +86,9 @@ __global__ void __launch_bounds__(TallCfg<T, NP>::THREADS, 2)
                 const int p = group_find(gp, item);
                 const TallArgs &a = gp.p[p].a;
                 const int64_t local = item - gp.p[p].item_begin;
-                const int64_t slab = local / a.splits;
-                const int64_t k0 = (local % a.splits) * a.kchunk;
+                int64_t slab, sp;
+                udivmod(local, a.splits, slab, sp);
+                const int64_t k0 = sp * a.kchunk;
                 const int64_t k1 = (k0 + a.kchunk < a.kp) ? k0 + a.kchunk : a.kp;
                 const T *Bp = static_cast<const T *>(a.Bp);
                 for (int64_t kk = k0; kk < k1; kk += Cfg::BKS, ++g) {
@@ -120,8 +121,9 @@ __global__ void __launch_bounds__(TallCfg<T, NP>::THREADS, 2)
         const int p = group_find(gp, item);
         const TallArgs &a = gp.p[p].a;
         const int64_t local = item - gp.p[p].item_begin;
-        const int64_t slab = local / a.splits;
-        const int split = (int)(local % a.splits);
+        int64_t slab, sp64;
+        udivmod(local, a.splits, slab, sp64);
+        const int split = (int)sp64;
         const int64_t k0 = (int64_t)split * a.kchunk;
         const int64_t k1 = (k0 + a.kchunk < a.kp) ? k0 + a.kchunk : a.kp;
 

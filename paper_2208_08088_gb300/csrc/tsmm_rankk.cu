@@ -117,8 +117,7 @@ struct RankEpilogue {
     Vec<T, V> c0v[4][2];
 
     __device__ __forceinline__ void load(const RankArgs &a, int64_t i0, int64_t tile, int tm, int tn,
-                                         bool vec_c, const T *sC) {
-        const T beta = static_cast<T>(a.beta);
+                                         bool vec_c, const T *sC, T beta) {
         const T *C = static_cast<const T *>(a.C);
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
@@ -149,9 +148,8 @@ struct RankEpilogue {
     // in FP64 the epilogue's arithmetic shares the FP64 pipe with the k
     // products of each output.
     __device__ __forceinline__ void store(const RankAcc<T> &acc, const RankArgs &a, int64_t i0,
-                                          int64_t tile, int tm, int tn, bool vec_c) const {
-        const T alpha = static_cast<T>(a.alpha);
-        const T beta = static_cast<T>(a.beta);
+                                          int64_t tile, int tm, int tn, bool vec_c, T alpha,
+                                          T beta) const {
         if (alpha == T(1)) store_t<true>(acc, a, i0, tile, tm, tn, vec_c, alpha, beta);
         else store_t<false>(acc, a, i0, tile, tm, tn, vec_c, alpha, beta);
     }
@@ -249,8 +247,9 @@ __global__ void __launch_bounds__(RankCfg<T>::CONSUMERS + 32, 2)
             int j = 0;      // tiles issued so far by this block
             bool ok = true;
             for (int64_t t = blockIdx.x; t < ntiles_total && ok; t += gridDim.x, ++j) {
-                const int64_t i0 = (t % mtiles) * Cfg::BMT;
-                const int64_t tile = t / mtiles;
+                int64_t tile, mt;
+                udivmod(t, mtiles, tile, mt);
+                const int64_t i0 = mt * Cfg::BMT;
                 if (want_c0) {
                     const int b = j % 2;
                     if (j >= 2 && !mbar_wait_bounded(&cempty[b], ((j / 2) & 1) ^ 1)) {
@@ -288,11 +287,14 @@ __global__ void __launch_bounds__(RankCfg<T>::CONSUMERS + 32, 2)
     const int tid = threadIdx.x;
     const int tm = tid % 16;
     const int tn = tid / 16;
+    const T ealpha = static_cast<T>(a.alpha);  // converted once, not per tile
+    const T ebeta = static_cast<T>(a.beta);
     int64_t g = 0;
     int j = 0;
     for (int64_t t = blockIdx.x; t < ntiles_total; t += gridDim.x, ++j) {
-        const int64_t i0 = (t % mtiles) * Cfg::BMT;
-        const int64_t tile = t / mtiles;
+        int64_t tile, mt;
+        udivmod(t, mtiles, tile, mt);
+        const int64_t i0 = mt * Cfg::BMT;
         RankAcc<T> acc;
         acc.zero();
         bool ok = true;
@@ -316,12 +318,12 @@ __global__ void __launch_bounds__(RankCfg<T>::CONSUMERS + 32, 2)
             if (lane == 0) atomicOr(status, kDevErrTimeout);
             return;  // this warp's part of the tile is not written; the host sees TSMM_ERR_TIMEOUT
         }
-        ep.load(a, i0, tile, tm, tn, vec_c, want_c0 ? sC + b * Cfg::C_TILE : nullptr);
+        ep.load(a, i0, tile, tm, tn, vec_c, want_c0 ? sC + b * Cfg::C_TILE : nullptr, ebeta);
         if (want_c0) {
             __syncwarp();
             if (lane == 0) mbar_arrive(&cempty[b]);  // C0 buffer b may be refilled
         }
-        ep.store(acc, a, i0, tile, tm, tn, vec_c);
+        ep.store(acc, a, i0, tile, tm, tn, vec_c, ealpha, ebeta);
     }
 }
 
@@ -347,6 +349,8 @@ __global__ void __launch_bounds__(256, 2) rankk_plain_kernel(const RankArgs a, b
 
     RankAcc<T> acc;
     acc.zero();
+    const T ealpha = static_cast<T>(a.alpha);
+    const T ebeta = static_cast<T>(a.beta);
 
     for (int64_t kc = 0; kc < a.k; kc += KC) {
         for (int e = tid * V; e < KC * BMT; e += Cfg::CONSUMERS * V) {
@@ -381,8 +385,8 @@ __global__ void __launch_bounds__(256, 2) rankk_plain_kernel(const RankArgs a, b
         __syncthreads();
     }
     RankEpilogue<T> ep;
-    ep.load(a, i0, tile, tm, tn, vec_c, nullptr);
-    ep.store(acc, a, i0, tile, tm, tn, vec_c);
+    ep.load(a, i0, tile, tm, tn, vec_c, nullptr, ebeta);
+    ep.store(acc, a, i0, tile, tm, tn, vec_c, ealpha, ebeta);
 }
 
 // FP32, k > 16 (FMA-bound, or near the ridge).  A 16-byte shared-memory load costs
@@ -532,8 +536,9 @@ __global__ void __launch_bounds__(WideCfg<TMA_EPI>::THREADS, 3)
             int j = 0;
             bool ok = true;
             for (int64_t t = blockIdx.x; t < ntiles_total && ok; t += gridDim.x, ++j) {
-                const int64_t i0 = (t % mtiles) * W::BMT;
-                const int64_t tile = t / mtiles;
+                int64_t tile, mt;
+                udivmod(t, mtiles, tile, mt);
+                const int64_t i0 = mt * W::BMT;
                 const float *Bt = static_cast<const float *>(a.Bp) + tile * a.kp * W::BNT;
                 for (int c = 0; c < nchunks; ++c, ++g) {
                     const int st = (int)(g % W::STAGES);
@@ -587,8 +592,9 @@ __global__ void __launch_bounds__(WideCfg<TMA_EPI>::THREADS, 3)
     bool ok = true;
     bool release_pending = false;  // thread 0: a store whose buffer is not yet freed
     for (int64_t t = blockIdx.x; t < ntiles_total && ok; t += gridDim.x, ++j) {
-        const int64_t i0 = (t % mtiles) * W::BMT;
-        const int64_t tile = t / mtiles;
+        int64_t tile, mt;
+        udivmod(t, mtiles, tile, mt);
+        const int64_t i0 = mt * W::BMT;
         WideAcc acc;
         acc.zero();
         for (int c = 0; c < nchunks; ++c, ++g) {

@@ -29,6 +29,8 @@ MIX = [  # (m, n, k, alpha, beta, a_offset)
     (333, 8, 100, 0.0, 1.5, 0),       # alpha = 0: scale launch
     (301, 5, 250, 1.0, 1.0, 1),       # unaligned A: plain-load launch
     (64, 64, 64, 1.0, 0.0, 0),
+    (900, 40, 1500, 1.0, 1.0, 0),     # width 48
+    (650, 24, 333, 1.5, 0.5, 0),      # width 24, with n = 17 above
 ]
 
 

@@ -51,6 +51,7 @@ CASES = [
     (1000, 64, 777, "uniform", 0, 0),
     (301, 5, 3000, "uniform", 2, 1),      # unaligned A: the plain-load kernel
     (32768, 8, 4096, "uniform", 0, 0),    # many slabs: split limited by the scratch
+    (700, 40, 3000, "uniform", 0, 0),     # width 48
 ]
 
 

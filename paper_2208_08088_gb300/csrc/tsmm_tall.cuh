@@ -132,14 +132,26 @@ __device__ __forceinline__ void tall_finish(T *red, const TallArgs &a, int64_t s
         named_barrier(1, Cfg::CONSUMERS);
     }
 
-    // C = alpha*v + beta*C0 for R rows of one column: the R C0 loads are
-    // issued together, ahead of the stores
+    // C = alpha*v + beta*C0 for R rows of one column: one vector access when
+    // the chunk lies inside C and is aligned, else the R C0 loads issued
+    // together, ahead of the stores
     auto store = [&](int q, const Vec<T, R> &v) {
         const int j = (q * R) / Cfg::BM;
         const int il = (q * R) % Cfg::BM;
         if (j >= a.n) return;
         T *c = static_cast<T *>(a.C) + row0 + il + (int64_t)j * a.ldc;
         const int64_t rows = a.m - (row0 + il);  // rows of this chunk inside C
+        if (rows >= R && reinterpret_cast<uintptr_t>(c) % sizeof(Vec<T, R>) == 0) {
+            Vec<T, R> o;
+            const Vec<T, R> c0 = beta != T(0) ? ld_vec<T, R>(c) : Vec<T, R>{};
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                o.v[r] = alpha * v.v[r];
+                if (beta != T(0)) o.v[r] = fma(beta, c0.v[r], o.v[r]);
+            }
+            st_vec<T, R>(c, o);
+            return;
+        }
         T c0[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) c0[r] = (beta != T(0) && r < rows) ? c[r] : T(0);

@@ -34,12 +34,17 @@ template <typename T, int NP>
 struct GroupCfg {
     using Tc = TallCfg<T, NP>;
     static constexpr int RED_BYTES = Tc::RED * (int)sizeof(T);
-    static constexpr int RING_BUDGET = 100 * 1024 - RED_BYTES;
+    // three blocks per SM where two ring stages and the reduction buffer fit in
+    // a third of the SM's shared memory (the FMA-bound FP32 widths 32 and 48:
+    // more warps to hide shared-memory latency), else two with a deeper ring
+    static constexpr bool THREE = sizeof(T) == 4 && (NP == 32 || NP == 48) &&
+                                  2 * Tc::STAGE_BYTES + RED_BYTES <= 72 * 1024;
+    static constexpr int RESIDENT = THREE ? 3 : 2;
+    static constexpr int RING_BUDGET = (THREE ? 72 : 100) * 1024 - RED_BYTES;
     static constexpr int STAGES_RAW = RING_BUDGET / Tc::STAGE_BYTES;
     static constexpr int STAGES = STAGES_RAW < 2 ? 2 : (STAGES_RAW > 6 ? 6 : STAGES_RAW);
     static constexpr int RING_BYTES = STAGES * Tc::STAGE_BYTES;
     static constexpr int SMEM = RING_BYTES + RED_BYTES + 2 * STAGES * 8 + 16;
-    static constexpr int RESIDENT = 2;
 };
 
 // Problem holding global item `item` (linear scan: at most kGroupMax problems).
@@ -50,7 +55,7 @@ __device__ __forceinline__ int group_find(const GroupParams &gp, int64_t item) {
 }
 
 template <typename T, int NP>
-__global__ void __launch_bounds__(TallCfg<T, NP>::THREADS, 2)
+__global__ void __launch_bounds__(TallCfg<T, NP>::THREADS, GroupCfg<T, NP>::RESIDENT)
     tall_grouped_kernel(const __grid_constant__ GroupParams gp) {
     using Cfg = TallCfg<T, NP>;
     using GC = GroupCfg<T, NP>;

@@ -263,7 +263,9 @@ TSMM_API tsmm_status tsmm_execute_grouped(const tsmm_group_item *items, int coun
  * beta = 0, so C is overwritten.  Blocks until the timing is done.  The
  * winning split count is recorded in the process-wide plan cache, which later
  * tsmm_plan calls for the same (dtype, m, n, k) on a GPU with the same SM count
- * reuse; a new plan with it is returned in *out.  Regime (ii) shapes have no
+ * reuse -- and, when no exact entry exists, calls for the same (dtype, n, k)
+ * whose m lies in the same quarter octave (2^(b/4) <= m < 2^((b+1)/4)); a new
+ * plan with it is returned in *out.  Regime (ii) shapes have no
  * tuned parameter yet and return the default plan.  Errors: as tsmm_plan and
  * tsmm_execute; INVALID_ARG for reps outside 1..1000.
  */
@@ -273,11 +275,13 @@ TSMM_API tsmm_status tsmm_autotune(int64_t m, int64_t n, int64_t k, tsmm_dtype d
 
 /*
  * The plan cache (the install-time record of tuned choices).  Text format, one
- * entry per line: `f32|f64 m n k sm_count splits`; lines starting with '#' are
- * comments.  If the environment variable TSMM_PLAN_CACHE names a file, it is
+ * entry per line: `f32|f64 m n k sm_count splits` for an exact m, or
+ * `f32q|f64q b n k sm_count splits` for every m of quarter-octave bucket b
+ * (b = floor(4 log2 m)); lines starting with '#' are comments.  If the environment variable TSMM_PLAN_CACHE names a file, it is
  * loaded on first use.  load merges a file into the cache (INVALID_ARG if the
  * file is missing or malformed, leaving the cache unchanged); save writes the
- * whole cache; clear empties it; size returns the number of entries.  The
+ * whole cache; clear empties it; size returns the number of entries (exact
+ * and bucket entries together).  The
  * cache is guarded by a mutex and shared by all threads of the process.
  */
 TSMM_API tsmm_status tsmm_plan_cache_load(const char *path);

@@ -4,9 +4,12 @@
 // and of its install-time stage, whose selection is made once per machine and
 // reused.  Here the candidates are split-K factors of the regime (i) kernel;
 // the winner is remembered in a process-wide cache keyed by (dtype, m, n, k,
-// SM count) that tsmm_plan consults, and that can be saved to and loaded from a
-// text file (TSMM_PLAN_CACHE names one to load on first use).
+// SM count) -- and by (dtype, quarter-octave bucket of m, n, k, SM count), so a
+// tuned choice also serves the other m of its bucket -- that tsmm_plan
+// consults, and that can be saved to and loaded from a text file
+// (TSMM_PLAN_CACHE names one to load on first use).
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <map>
@@ -27,14 +30,20 @@ namespace {
 using Key = std::tuple<int, int64_t, int64_t, int64_t, int>;
 
 std::mutex g_cache_mu;
-std::map<Key, int> g_cache;
+std::map<Key, int> g_cache;   // exact m
+std::map<Key, int> g_bucket;  // m replaced by its bucket
 bool g_env_loaded = false;
+
+// quarter-octave bucket of m >= 1: floor(4 log2 m); 2^(b/4) <= m < 2^((b+1)/4)
+int64_t m_bucket(int64_t m) {
+    return m < 1 ? -1 : (int64_t)std::floor(4.0 * std::log2((double)m) + 1e-9);
+}
 
 tsmm_status load_file_locked(const char *path) {
     FILE *f = std::fopen(path, "r");
     if (!f) return TSMM_ERR_INVALID_ARG;
     char line[512];
-    std::map<Key, int> parsed;
+    std::map<Key, int> parsed, parsed_b;
     bool bad = false;
     while (std::fgets(line, sizeof line, f)) {
         if (line[0] == '#' || line[0] == '\n' || line[0] == '\0') continue;
@@ -46,20 +55,23 @@ tsmm_status load_file_locked(const char *path) {
             bad = true;
             break;
         }
+        const std::string t(dt);
+        const bool bucket = t == "f32q" || t == "f64q";
         int d;
-        if (std::string(dt) == "f32")
+        if (t == "f32" || t == "f32q")
             d = TSMM_F32;
-        else if (std::string(dt) == "f64")
+        else if (t == "f64" || t == "f64q")
             d = TSMM_F64;
         else {
             bad = true;
             break;
         }
-        parsed[Key(d, m, n, k, sms)] = splits;
+        (bucket ? parsed_b : parsed)[Key(d, m, n, k, sms)] = splits;
     }
     std::fclose(f);
     if (bad) return TSMM_ERR_INVALID_ARG;
     for (auto &kv : parsed) g_cache[kv.first] = kv.second;
+    for (auto &kv : parsed_b) g_bucket[kv.first] = kv.second;
     return TSMM_OK;
 }
 
@@ -78,13 +90,16 @@ int plan_cache_lookup(tsmm_dtype dtype, int64_t m, int64_t n, int64_t k, int sms
     std::lock_guard<std::mutex> lock(g_cache_mu);
     load_env_once_locked();
     auto it = g_cache.find(Key(dtype, m, n, k, sms));
-    return it == g_cache.end() ? 0 : it->second;
+    if (it != g_cache.end()) return it->second;
+    auto ib = g_bucket.find(Key(dtype, m_bucket(m), n, k, sms));
+    return ib == g_bucket.end() ? 0 : ib->second;
 }
 
 void plan_cache_store(tsmm_dtype dtype, int64_t m, int64_t n, int64_t k, int sms, int splits) {
     std::lock_guard<std::mutex> lock(g_cache_mu);
     load_env_once_locked();
     g_cache[Key(dtype, m, n, k, sms)] = splits;
+    g_bucket[Key(dtype, m_bucket(m), n, k, sms)] = splits;
 }
 
 }  // namespace tsmm
@@ -103,9 +118,15 @@ tsmm_status tsmm_plan_cache_save(const char *path) {
     std::lock_guard<std::mutex> lock(g_cache_mu);
     FILE *f = std::fopen(path, "w");
     if (!f) return TSMM_ERR_INVALID_ARG;
-    std::fprintf(f, "# tsmm plan cache v1: dtype m n k sm_count splits\n");
+    std::fprintf(f, "# tsmm plan cache v2: dtype m n k sm_count splits (dtype f32q/f64q: m is a "
+                    "quarter-octave bucket)\n");
     for (auto &kv : g_cache) {
         std::fprintf(f, "%s %lld %lld %lld %d %d\n", std::get<0>(kv.first) == TSMM_F64 ? "f64" : "f32",
+                     (long long)std::get<1>(kv.first), (long long)std::get<2>(kv.first),
+                     (long long)std::get<3>(kv.first), std::get<4>(kv.first), kv.second);
+    }
+    for (auto &kv : g_bucket) {
+        std::fprintf(f, "%s %lld %lld %lld %d %d\n", std::get<0>(kv.first) == TSMM_F64 ? "f64q" : "f32q",
                      (long long)std::get<1>(kv.first), (long long)std::get<2>(kv.first),
                      (long long)std::get<3>(kv.first), std::get<4>(kv.first), kv.second);
     }
@@ -117,13 +138,14 @@ tsmm_status tsmm_plan_cache_clear(void) {
     std::lock_guard<std::mutex> lock(g_cache_mu);
     g_env_loaded = true;  // an explicit clear also drops the environment's file
     g_cache.clear();
+    g_bucket.clear();
     return TSMM_OK;
 }
 
 int64_t tsmm_plan_cache_size(void) {
     std::lock_guard<std::mutex> lock(g_cache_mu);
     load_env_once_locked();
-    return (int64_t)g_cache.size();
+    return (int64_t)(g_cache.size() + g_bucket.size());
 }
 
 tsmm_status tsmm_autotune(int64_t m, int64_t n, int64_t k, tsmm_dtype dtype, const void *A_dev,

@@ -83,20 +83,21 @@ def test_plan_cache_file_roundtrip(tmp_path):
     tsmm.tsmm_plan_cache_clear()
     assert tsmm.tsmm_plan_cache_size() == 0
     src = tmp_path / "cache.txt"
-    src.write_text("# comment\nf32 32768 16 32768 152 19\nf64 4096 8 4096 152 3\n\n")
+    src.write_text("# comment\nf32 32768 16 32768 152 19\nf64 4096 8 4096 152 3\nf32q 60 16 32768 152 7\n\n")
     tsmm.tsmm_plan_cache_load(str(src))
-    assert tsmm.tsmm_plan_cache_size() == 2
+    assert tsmm.tsmm_plan_cache_size() == 3
     dst = tmp_path / "out.txt"
     tsmm.tsmm_plan_cache_save(str(dst))
     lines = [l for l in dst.read_text().splitlines() if not l.startswith("#")]
-    assert sorted(lines) == sorted(["f32 32768 16 32768 152 19", "f64 4096 8 4096 152 3"])
+    assert sorted(lines) == sorted(["f32 32768 16 32768 152 19", "f64 4096 8 4096 152 3",
+                                    "f32q 60 16 32768 152 7"])
     bad = tmp_path / "bad.txt"
     bad.write_text("f16 1 2 3 4 5\n")
     with pytest.raises(tsmm.TsmmError):
         tsmm.tsmm_plan_cache_load(str(bad))
     with pytest.raises(tsmm.TsmmError):
         tsmm.tsmm_plan_cache_load(str(tmp_path / "missing.txt"))
-    assert tsmm.tsmm_plan_cache_size() == 2
+    assert tsmm.tsmm_plan_cache_size() == 3
     tsmm.tsmm_plan_cache_clear()
     assert tsmm.tsmm_plan_cache_size() == 0
 

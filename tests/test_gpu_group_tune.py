@@ -100,9 +100,11 @@ def test_autotune_records_and_reuses_plan(tmp_path):
     dC = to_device(np.zeros((m, n), dtype=np.float32, order="F"))
     tuned = tsmm.autotune(dA, pb, dC, reps=3)
     splits = tuned.info()["splits"]
-    assert tsmm.tsmm_plan_cache_size() == 1
-    # tsmm_plan now returns the tuned choice for this shape
+    assert tsmm.tsmm_plan_cache_size() == 2  # the exact entry and its m bucket
+    # tsmm_plan now returns the tuned choice for this shape, and for another m
+    # of the same quarter octave (2048 <= m < 2435)
     assert tsmm.plan(m, n, k, torch.float32).info()["splits"] == splits
+    assert tsmm.plan(2300, n, k, torch.float32).info()["splits"] == splits
     # the tuned plan is correct (integer inputs: bit-exact)
     dC = to_device(C0)
     tsmm.execute(tuned, 1.5, dA, pb, 0.5, dC)

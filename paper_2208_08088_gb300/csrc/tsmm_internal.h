@@ -131,15 +131,17 @@ struct RankArgs {
     int num_sms;     // persistent grid size = resident blocks x SMs
 };
 // tmA: tensor map of A (box bm x 32) or nullptr for the plain-load kernel;
-// The FP32 regime (ii) kernel for k > kRankWideMinK - 1 streams k in chunks of kRankWideKC (its A
-// tensor map box is bm x kRankWideKC; every other kernel's is bm x kTallBKS).
-constexpr int kRankWideKC = 16;
-constexpr int kRankWideMinK = kRankWideKC + 1;  // at least two chunks
+// The FP32 regime (ii) kernel for k >= kRankWideMinK streams k in chunks of
+// rank_wide_kc(k): 16 up to k = 32 (three blocks per SM), 32 above (two blocks
+// per SM), so that every tile has at least two chunks.  Its A tensor map box is
+// bm x rank_wide_kc(k); every other kernel's is bm x kTallBKS.
+constexpr int kRankWideMinK = 17;
+constexpr int rank_wide_kc(int64_t k) { return k <= 32 ? 16 : 32; }
 inline bool rank_wide(tsmm_dtype d, int regime, int precision, int64_t k) {
     return d == TSMM_F32 && regime == 2 && precision == 0 && k >= kRankWideMinK;
 }
 inline int a_box_k(tsmm_dtype d, int regime, int precision, int64_t k) {
-    return rank_wide(d, regime, precision, k) ? kRankWideKC : kTallBKS;
+    return rank_wide(d, regime, precision, k) ? rank_wide_kc(k) : kTallBKS;
 }
 // tmC: tensor map of C (box bm x kRankNT) when C meets the TMA rules, else nullptr.
 cudaError_t launch_rankk(tsmm_dtype dt, const CUtensorMap *tmA, const CUtensorMap *tmC,

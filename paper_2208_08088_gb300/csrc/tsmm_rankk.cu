@@ -389,16 +389,20 @@ __global__ void __launch_bounds__(256, 2) rankk_plain_kernel(const RankArgs a, b
     ep.store(acc, a, i0, tile, tm, tn, vec_c, ealpha, ebeta);
 }
 
-// FP32, k > 16 (FMA-bound, or near the ridge).  A 16-byte shared-memory load costs
+// FP32, k > 32 (FMA-bound).  A 16-byte shared-memory load costs
 // four wavefronts whatever its address pattern, and the SM serves one per
 // cycle; the 8 x 4 register tiles above need 1.5 per cycle at the FMA peak,
 // so this kernel uses 8 x 8 tiles (1.0 per cycle): 4 consumer warps own the
 // same 128 x 64 C tile as a 2 x 2 grid of 64 x 32 warp tiles, lane
 // (lm = lane % 8, ln = lane / 8) owning rows {wm*64 + lm*4 + r, +32} and
 // columns {wn*32 + ln*4 + c, +16} (r, c < 4); a warp's A reads cover one
-// 128-byte line, its B reads 64 bytes.  To keep three blocks (12 consumer
-// warps) per SM in 227 KB, k streams in chunks of 16 through 3 stages
-// (12 KB each) and the C tile has one 32 KB buffer.
+// 128-byte line, its B reads 64 bytes.  For k > 32, k streams in chunks of 32
+// through 3 stages (24 KB each) and the C tile has one 32 KB buffer: two blocks
+// (8 consumer warps) per SM, each chunk unrolled whole.  Chunks of 16 (3 stages
+// of 12 KB) fit three blocks per SM, but each chunk's wait and release costs a
+// fixed stretch of issue: their main loop ran at ~0.72 of the FMA peak against
+// ~0.79 for chunks of 32.  For k in 17..32 the chunks of 16 stay (two chunks
+// per tile, so the C0 copy overlaps the second).
 //
 // TMA_EPI (C meets the TMA rules): the producer brings the C0 tile into the
 // buffer with one tensor copy while the tile's products run; the epilogue
@@ -406,11 +410,12 @@ __global__ void __launch_bounds__(256, 2) rankk_plain_kernel(const RankArgs a, b
 // out with a TMA store and frees the buffer once the store has read it.
 // Otherwise the epilogue moves C0 and C with 16-byte loads and stores.
 namespace {
-template <bool TMA_EPI>
+template <bool TMA_EPI, int KC_>
 struct WideCfg {
     static constexpr int BMT = 128;
     static constexpr int BNT = kRankNT;  // 64
-    static constexpr int KC = kRankWideKC;
+    static constexpr int KC = KC_;
+    static constexpr int RESIDENT = KC == 16 ? 3 : 2;  // blocks per SM
     static constexpr int STAGES = 3;
     static constexpr int CONSUMERS = 128;
     static constexpr int THREADS = CONSUMERS + 32;
@@ -421,7 +426,7 @@ struct WideCfg {
     static constexpr int DATA_BYTES = (STAGES * STAGE_ELEMS + C_ELEMS) * 4;
     static constexpr int NBAR = 2 * STAGES + 3;
     static constexpr int SMEM = DATA_BYTES + NBAR * 8 + 16;
-    static_assert(3 * (SMEM + 1024) <= 228 * 1024, "three blocks per SM");
+    static_assert(RESIDENT * (SMEM + 1024) <= 228 * 1024, "resident blocks per SM");
 };
 
 struct WideAcc {
@@ -453,7 +458,7 @@ struct WideAcc {
     template <int KC>
     __device__ __forceinline__ void chunk(const float *As, const float *Bs, int kcnt, int r0, int c0) {
         if (kcnt == KC) {
-#pragma unroll 8
+#pragma unroll(KC == 16 ? 8 : KC)
             for (int pc = 0; pc < KC; ++pc) step(As, Bs, pc, r0, c0);
         } else {
 #pragma unroll 4
@@ -492,11 +497,11 @@ __device__ __forceinline__ void tma_store_2d_commit(const void *tmap, const void
 }
 }  // namespace
 
-template <bool TMA_EPI>
-__global__ void __launch_bounds__(WideCfg<TMA_EPI>::THREADS, 3)
+template <bool TMA_EPI, int KC>
+__global__ void __launch_bounds__(WideCfg<TMA_EPI, KC>::THREADS, WideCfg<TMA_EPI, KC>::RESIDENT)
     rankk_wide_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmC,
                       const RankArgs a, bool vec_c, unsigned *status) {
-    using W = WideCfg<TMA_EPI>;
+    using W = WideCfg<TMA_EPI, KC>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float *sStage = reinterpret_cast<float *>(smem_raw);
     float *cbuf = sStage + W::STAGES * W::STAGE_ELEMS;
@@ -698,21 +703,21 @@ __global__ void __launch_bounds__(WideCfg<TMA_EPI>::THREADS, 3)
     if (TMA_EPI && threadIdx.x == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
 }
 
-template <bool TMA_EPI>
+template <bool TMA_EPI, int KC>
 static cudaError_t launch_rankk_wide_t(const CUtensorMap *tmA, const CUtensorMap *tmC, const RankArgs &a,
                                        bool vec_c, unsigned *status, cudaStream_t s) {
-    using W = WideCfg<TMA_EPI>;
+    using W = WideCfg<TMA_EPI, KC>;
     static bool attr_done = false;
     if (!attr_done) {
-        cudaError_t e = cudaFuncSetAttribute(rankk_wide_kernel<TMA_EPI>,
+        cudaError_t e = cudaFuncSetAttribute(rankk_wide_kernel<TMA_EPI, KC>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, W::SMEM);
         if (e != cudaSuccess) return e;
         attr_done = true;
     }
     const int64_t tiles = ((a.m + W::BMT - 1) / W::BMT) * ((a.n + W::BNT - 1) / W::BNT);
-    const int64_t slots = 3 * (int64_t)(a.num_sms > 0 ? a.num_sms : 1);
+    const int64_t slots = W::RESIDENT * (int64_t)(a.num_sms > 0 ? a.num_sms : 1);
     const unsigned grid = (unsigned)(tiles < slots ? tiles : slots);
-    rankk_wide_kernel<TMA_EPI><<<grid, W::THREADS, W::SMEM, s>>>(*tmA, *tmC, a, vec_c, status);
+    rankk_wide_kernel<TMA_EPI, KC><<<grid, W::THREADS, W::SMEM, s>>>(*tmA, *tmC, a, vec_c, status);
     return cudaGetLastError();
 }
 
@@ -745,10 +750,15 @@ static cudaError_t launch_rankk_t(const CUtensorMap *tmA, const CUtensorMap *tmC
     const bool vec_c = (reinterpret_cast<uintptr_t>(a.C) % 16 == 0) &&
                        ((a.ldc * (int64_t)sizeof(T)) % 16 == 0);
     if (tmA) {
-        // FP32 from k = kRankWideMinK on: the 8 x 8-tile kernel (its A tensor map has a 128 x 16 box)
-        if (rank_wide(sizeof(T) == 4 ? TSMM_F32 : TSMM_F64, 2, 0, a.k))
-            return tmC ? launch_rankk_wide_t<true>(tmA, tmC, a, vec_c, status, s)
-                       : launch_rankk_wide_t<false>(tmA, tmA, a, vec_c, status, s);
+        // FP32 from k = kRankWideMinK on: the 8 x 8-tile kernel (its A tensor map's box is
+        // 128 x rank_wide_kc(k))
+        if (rank_wide(sizeof(T) == 4 ? TSMM_F32 : TSMM_F64, 2, 0, a.k)) {
+            if (rank_wide_kc(a.k) == 16)
+                return tmC ? launch_rankk_wide_t<true, 16>(tmA, tmC, a, vec_c, status, s)
+                           : launch_rankk_wide_t<false, 16>(tmA, tmA, a, vec_c, status, s);
+            return tmC ? launch_rankk_wide_t<true, 32>(tmA, tmC, a, vec_c, status, s)
+                       : launch_rankk_wide_t<false, 32>(tmA, tmA, a, vec_c, status, s);
+        }
         // output-bound shapes: one k chunk, C0 prefetched by TMA when it is read
         if (a.k <= Cfg::KC) {
             if (tmC && a.beta != 0.0) return launch_rankk_tma_t<T, 1, true>(tmA, tmC, a, vec_c, status, s);

@@ -406,8 +406,11 @@ __global__ void __launch_bounds__(256, 2) rankk_plain_kernel(const RankArgs a, b
 //
 // TMA_EPI (C meets the TMA rules): the producer brings the C0 tile into the
 // buffer with one tensor copy while the tile's products run; the epilogue
-// overwrites it in place with alpha*acc + beta*C0, and one thread writes it
-// out with a TMA store and frees the buffer once the store has read it.
+// overwrites it in place with alpha*acc + beta*C0.  The producer then writes it
+// out with a TMA store and, once the store has read the buffer, issues the next
+// tile's C0 copy into it -- from the next tile's second chunk on, so the copy has
+// that tile's chunks to land (without it, the copy issued one chunk before the
+// epilogue was still in flight at half of the k = 64 epilogues).
 // Otherwise the epilogue moves C0 and C with 16-byte loads and stores.
 namespace {
 template <bool TMA_EPI, int KC_>
@@ -424,7 +427,7 @@ struct WideCfg {
     static constexpr int STAGE_ELEMS = A_CHUNK + B_CHUNK;
     static constexpr int C_ELEMS = TMA_EPI ? BMT * BNT : 0;  // [BNT][BMT], as the tensor copy lays it out
     static constexpr int DATA_BYTES = (STAGES * STAGE_ELEMS + C_ELEMS) * 4;
-    static constexpr int NBAR = 2 * STAGES + 3;
+    static constexpr int NBAR = 2 * STAGES + 2;
     static constexpr int SMEM = DATA_BYTES + NBAR * 8 + 16;
     static_assert(RESIDENT * (SMEM + 1024) <= 228 * 1024, "resident blocks per SM");
 };
@@ -509,7 +512,6 @@ __global__ void __launch_bounds__(WideCfg<TMA_EPI, KC>::THREADS, WideCfg<TMA_EPI
     uint64_t *empty = full + W::STAGES;
     uint64_t *cfull = empty + W::STAGES;  // C0 landed (or buffer free, beta == 0)
     uint64_t *cstore = cfull + 1;         // results written (4 consumer warps)
-    uint64_t *cempty = cstore + 1;        // the store has read the buffer
 
     const int warp = threadIdx.x / 32;
     const int lane = threadIdx.x % 32;
@@ -527,7 +529,6 @@ __global__ void __launch_bounds__(WideCfg<TMA_EPI, KC>::THREADS, WideCfg<TMA_EPI
         }
         mbar_init(cfull, 1);
         mbar_init(cstore, W::CONSUMERS / 32);
-        mbar_init(cempty, 1);
         fence_mbar_init();
     }
     __syncthreads();
@@ -540,6 +541,15 @@ __global__ void __launch_bounds__(WideCfg<TMA_EPI, KC>::THREADS, WideCfg<TMA_EPI
             int64_t g = 0;
             int j = 0;
             bool ok = true;
+            int32_t prev_x = 0, prev_y = 0;  // C coordinates of the previous tile
+            // write tile j's results out (they are complete once every consumer warp
+            // arrived on cstore) and wait until the store has read the buffer
+            auto store_tile = [&](int jj, int32_t x, int32_t y) -> bool {
+                if (!mbar_wait_bounded(cstore, (uint32_t)(jj & 1))) return false;
+                tma_store_2d_commit(&tmC, cbuf, x, y);
+                asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+                return true;
+            };
             for (int64_t t = blockIdx.x; t < ntiles_total && ok; t += gridDim.x, ++j) {
                 int64_t tile, mt;
                 udivmod(t, mtiles, tile, mt);
@@ -558,14 +568,16 @@ __global__ void __launch_bounds__(WideCfg<TMA_EPI, KC>::THREADS, WideCfg<TMA_EPI
                     mbar_arrive_expect_tx(&full[st], (W::A_CHUNK + brows * W::BNT) * 4);
                     tma_load_2d(sA, &tmA, (int32_t)i0, (int32_t)kc, &full[st], pol_keep);
                     bulk_load(sA + W::A_CHUNK, Bt + kc * W::BNT, brows * W::BNT * 4, &full[st], pol_keep);
-                    // the C0 tile follows the tile's second chunk (k >= kRankWideMinK: there
-                    // always is one), so two chunks are in flight while the previous
-                    // tile's store drains
+                    // after the tile's second chunk (k >= kRankWideMinK: there always is
+                    // one): the previous tile's store, then this tile's C0
                     if (TMA_EPI && c == 1) {
-                        if (j >= 1 && !mbar_wait_bounded(cempty, (uint32_t)((j - 1) & 1))) {
+                        if (j >= 1 && !store_tile(j - 1, prev_x, prev_y)) {
+                            ++g;  // this chunk is in flight: the drain below waits for it
                             ok = false;
                             break;
                         }
+                        prev_x = (int32_t)i0;
+                        prev_y = (int32_t)(tile * W::BNT);
                         if (use_c0) {
                             mbar_arrive_expect_tx(cfull, W::C_ELEMS * 4);
                             tma_load_2d(cbuf, &tmC, (int32_t)i0, (int32_t)(tile * W::BNT), cfull, pol_stream);
@@ -575,11 +587,14 @@ __global__ void __launch_bounds__(WideCfg<TMA_EPI, KC>::THREADS, WideCfg<TMA_EPI
                     }
                 }
             }
+            // the last tile's store
+            if (TMA_EPI && ok && j >= 1 && !store_tile(j - 1, prev_x, prev_y)) ok = false;
             if (!ok) atomicOr(status, kDevErrTimeout);
             // copies in flight land before the block may exit
             for (int64_t q = g > W::STAGES ? g - W::STAGES : 0; q < g; ++q)
                 mbar_wait_bounded(&full[q % W::STAGES], (uint32_t)((q / W::STAGES) & 1));
             if (TMA_EPI && j >= 1) mbar_wait_bounded(cfull, (uint32_t)((j - 1) & 1));
+            if (TMA_EPI) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
         }
         return;
     }
@@ -595,7 +610,6 @@ __global__ void __launch_bounds__(WideCfg<TMA_EPI, KC>::THREADS, WideCfg<TMA_EPI
     int64_t g = 0;
     int j = 0;
     bool ok = true;
-    bool release_pending = false;  // thread 0: a store whose buffer is not yet freed
     for (int64_t t = blockIdx.x; t < ntiles_total && ok; t += gridDim.x, ++j) {
         int64_t tile, mt;
         udivmod(t, mtiles, tile, mt);
@@ -614,14 +628,6 @@ __global__ void __launch_bounds__(WideCfg<TMA_EPI, KC>::THREADS, WideCfg<TMA_EPI
             acc.chunk<W::KC>(sA, sA + W::A_CHUNK, kcnt, r0, c0);
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty[st]);
-            if (TMA_EPI && release_pending) {
-                // one chunk after the previous tile's store was issued it has read
-                // the buffer long since: free it for the next C0 (the producer
-                // asks for it after this tile's second chunk)
-                asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
-                mbar_arrive(cempty);
-                release_pending = false;
-            }
         }
         if (!ok) break;
         if (TMA_EPI) {
@@ -639,19 +645,10 @@ __global__ void __launch_bounds__(WideCfg<TMA_EPI, KC>::THREADS, WideCfg<TMA_EPI
                     *p = axpby4(alpha, acc.rows(rg, cc), beta, c0v, use_c0);
                 }
             }
+            // results in the buffer, visible to the tensor copy: the producer stores them
             fence_proxy_async_smem();
             __syncwarp();
             if (lane == 0) mbar_arrive(cstore);
-            if (threadIdx.x == 0) {
-                // every warp's results are in: write the tile; the buffer is freed
-                // after this thread's next chunk
-                if (!mbar_wait_bounded(cstore, (uint32_t)(j & 1))) {
-                    ok = false;
-                } else {
-                    tma_store_2d_commit(&tmC, cbuf, (int32_t)i0, (int32_t)(tile * W::BNT));
-                    release_pending = true;
-                }
-            }
             continue;
         }
         // plain epilogue in two halves of 4 columns: all C0 loads of a half before its stores
@@ -700,7 +697,6 @@ __global__ void __launch_bounds__(WideCfg<TMA_EPI, KC>::THREADS, WideCfg<TMA_EPI
         }
     }
     if (!ok && lane == 0) atomicOr(status, kDevErrTimeout);
-    if (TMA_EPI && threadIdx.x == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
 }
 
 template <bool TMA_EPI, int KC>

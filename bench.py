@@ -57,6 +57,7 @@ def parse():
     p.add_argument("--workload", choices=["tall", "rankk", "precision", "serving"], default="tall")
     p.add_argument("--requests", type=int, default=10000, help="serving: number of requests")
     p.add_argument("--load", type=float, default=0.8, help="serving: arrival rate / measured capacity")
+    p.add_argument("--streams", type=int, default=4, help="serving: the server's CUDA streams")
     p.add_argument("--precision", choices=["native", "bf16x3"], default="native",
                    help="arithmetic of the tall sweep: IEEE FMA (default) or the BF16x3 tensor-core mode")
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
@@ -733,7 +734,7 @@ def run_serving(args):
     tune_s = time.time() - t_tune
 
     budget = 40 << 30
-    srv = tsmm.Server(budget_bytes=budget, num_streams=4, max_batch=48, arena_bytes=1 << 30)
+    srv = tsmm.Server(budget_bytes=budget, num_streams=args.streams, max_batch=48, arena_bytes=1 << 30)
 
     def session(arrivals):
         arr = requests(arrivals)
@@ -758,6 +759,7 @@ def run_serving(args):
     comps = session(arrivals)
     lat = np.array([c["complete_s"] - c["arrival_s"] for c in comps])
     qwait = np.array([c["admit_s"] - c["arrival_s"] for c in comps])
+    lwait = np.array([c["launch_s"] - c["arrival_s"] for c in comps])
     span = max(c["complete_s"] for c in comps) - min(c["arrival_s"] for c in comps)
     srv.close()
     line = {"metric": METRIC, "value": round(fl.sum() / span / 1e9, 1), "unit": UNIT, "n_gpus": 1,
@@ -766,7 +768,7 @@ def run_serving(args):
             "config": {"workload": f"serving: {N} FP32 TSMM requests, Poisson arrivals at "
                                    f"{args.load:.2f} x measured capacity, m log-uniform [1024, 262144], "
                                    "32 resident packed B with k log-uniform [64, 8192], n log-uniform "
-                                   "[1, 64]; 40 GB admission budget; grouped persistent launches on 4 streams",
+                                   f"[1, 64]; 40 GB admission budget; grouped persistent launches on {args.streams} streams",
                        "total_gflop": round(fl.sum() / 1e9, 1),
                        "plans": f"autotuned: {len(seen)} shapes (one per packed B and quarter octave of m), "
                                 f"{tune_s:.1f} s, before the sessions"},
@@ -774,7 +776,9 @@ def run_serving(args):
                            "p90": round(float(np.percentile(lat, 90)) * 1e3, 3),
                            "p99": round(float(np.percentile(lat, 99)) * 1e3, 3),
                            "mean": round(float(lat.mean()) * 1e3, 3),
-                           "queue_wait_p99": round(float(np.percentile(qwait, 99)) * 1e3, 3)},
+                           "queue_wait_p99": round(float(np.percentile(qwait, 99)) * 1e3, 3),
+                           "launch_wait_p50": round(float(np.percentile(lwait, 50)) * 1e3, 3),
+                           "launch_wait_p99": round(float(np.percentile(lwait, 99)) * 1e3, 3)},
             "capacity": {"requests_per_s": round(capacity, 1), "gflops": round(cap_gflops, 1),
                          "makespan_ms": round(makespan * 1e3, 2)},
             "arrival_rate_per_s": round(lam, 1)}

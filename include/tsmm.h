@@ -296,10 +296,17 @@ TSMM_API int64_t tsmm_plan_cache_size(void);
  * requests once their arrival time (on the tsmm_server_clock clock) has
  * passed, admits them in arrival order while the device memory that admitted,
  * unfinished requests pin -- A (m x k), C (m x n) and the split-K workspace --
- * stays within budget_bytes, and launches every group of admitted requests
- * with tsmm_execute_grouped on one of num_streams streams as soon as a stream
- * is free: requests admitted while earlier batches run form the next batch and
- * overlap with them on the device.  Completion is detected with CUDA events.
+ * stays within budget_bytes, and launches every group of admitted requests on
+ * one of num_streams lanes as soon as a lane is free: requests admitted while
+ * earlier batches run form the next batch and overlap with them on the device.
+ * A batch runs cheapest request first, as up to six grouped sub-batches of
+ * growing size with one completion event each (CUDA events), so a small
+ * request completes with its sub-batch rather than with the whole batch.  A
+ * lane is three high-priority streams and one low-priority stream: the first
+ * sub-batch runs as persistent grouped launches, one per kernel class, spread
+ * over the high-priority streams; the others run one thread block per work
+ * item on the low-priority stream, so newly launched small work gets SMs as
+ * items finish.
  * Each request's plan depends only on its shape, so its result is the same bit
  * for bit alone or in any mix.  The caller owns A, C and the packed B, and must
  * keep them alive until the request's completion has been polled.
@@ -310,7 +317,7 @@ typedef struct tsmm_server_config {
     size_t budget_bytes;  /* device memory admitted, unfinished requests may pin (> 0) */
     size_t arena_bytes;   /* split-K workspace arena allocated once (0 = 256 MiB); a request's
                              workspace is capped at a quarter of it */
-    int num_streams;      /* batches that may run concurrently, 1..16 */
+    int num_streams;      /* lanes (batches that may run concurrently), 1..16 */
     int max_batch;        /* requests per launch group, 1..1024 */
     tsmm_dtype dtype;     /* every request's dtype */
 } tsmm_server_config;

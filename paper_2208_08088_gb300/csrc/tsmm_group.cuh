@@ -12,6 +12,7 @@
 // Split-K partials are finished by the last-arriving block per slab, as in
 // the single-problem kernel, using each problem's own plan workspace.
 #pragma once
+#include <climits>
 #include "tsmm_tall.cuh"
 
 namespace tsmm {
@@ -172,8 +173,10 @@ __global__ void __launch_bounds__(TallCfg<T, NP>::THREADS, GroupCfg<T, NP>::RESI
     }
 }
 
+// persistent: RESIDENT blocks per SM loop over the items; otherwise one block
+// per item, so that blocks of higher-priority streams get SMs as items finish.
 template <typename T, int NP>
-cudaError_t launch_grouped_t(const GroupParams &gp, int num_sms, cudaStream_t s) {
+cudaError_t launch_grouped_t(const GroupParams &gp, int num_sms, bool persistent, cudaStream_t s) {
     using GC = GroupCfg<T, NP>;
     static bool attr_done = false;
     if (!attr_done) {
@@ -182,7 +185,7 @@ cudaError_t launch_grouped_t(const GroupParams &gp, int num_sms, cudaStream_t s)
         if (e != cudaSuccess) return e;
         attr_done = true;
     }
-    const int64_t slots = (int64_t)GC::RESIDENT * (num_sms > 0 ? num_sms : 1);
+    const int64_t slots = persistent ? (int64_t)GC::RESIDENT * (num_sms > 0 ? num_sms : 1) : INT_MAX;
     const unsigned grid = (unsigned)(gp.total_items < slots ? gp.total_items : slots);
     if (grid == 0) return cudaSuccess;
     tall_grouped_kernel<T, NP><<<grid, TallCfg<T, NP>::THREADS, GC::SMEM, s>>>(gp);
@@ -190,17 +193,18 @@ cudaError_t launch_grouped_t(const GroupParams &gp, int num_sms, cudaStream_t s)
 }
 
 template <typename T>
-cudaError_t launch_grouped_dispatch(int np, const GroupParams &gp, int num_sms, cudaStream_t s) {
+cudaError_t launch_grouped_dispatch(int np, const GroupParams &gp, int num_sms, bool persistent,
+                                    cudaStream_t s) {
     switch (np) {
-        case 1: return launch_grouped_t<T, 1>(gp, num_sms, s);
-        case 2: return launch_grouped_t<T, 2>(gp, num_sms, s);
-        case 4: return launch_grouped_t<T, 4>(gp, num_sms, s);
-        case 8: return launch_grouped_t<T, 8>(gp, num_sms, s);
-        case 16: return launch_grouped_t<T, 16>(gp, num_sms, s);
-        case 24: return launch_grouped_t<T, 24>(gp, num_sms, s);
-        case 32: return launch_grouped_t<T, 32>(gp, num_sms, s);
-        case 48: return launch_grouped_t<T, 48>(gp, num_sms, s);
-        case 64: return launch_grouped_t<T, 64>(gp, num_sms, s);
+        case 1: return launch_grouped_t<T, 1>(gp, num_sms, persistent, s);
+        case 2: return launch_grouped_t<T, 2>(gp, num_sms, persistent, s);
+        case 4: return launch_grouped_t<T, 4>(gp, num_sms, persistent, s);
+        case 8: return launch_grouped_t<T, 8>(gp, num_sms, persistent, s);
+        case 16: return launch_grouped_t<T, 16>(gp, num_sms, persistent, s);
+        case 24: return launch_grouped_t<T, 24>(gp, num_sms, persistent, s);
+        case 32: return launch_grouped_t<T, 32>(gp, num_sms, persistent, s);
+        case 48: return launch_grouped_t<T, 48>(gp, num_sms, persistent, s);
+        case 64: return launch_grouped_t<T, 64>(gp, num_sms, persistent, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -17,8 +17,8 @@
 #include "tsmm_group.cuh"
 
 namespace tsmm {
-cudaError_t launch_grouped_f32(int np, const GroupParams &gp, int num_sms, cudaStream_t s);
-cudaError_t launch_grouped_f64(int np, const GroupParams &gp, int num_sms, cudaStream_t s);
+cudaError_t launch_grouped_f32(int np, const GroupParams &gp, int num_sms, bool persistent, cudaStream_t s);
+cudaError_t launch_grouped_f64(int np, const GroupParams &gp, int num_sms, bool persistent, cudaStream_t s);
 }  // namespace tsmm
 
 using namespace tsmm;
@@ -73,8 +73,8 @@ bool groupable(const tsmm_group_item &it) {
 
 }  // namespace
 
-extern "C" tsmm_status tsmm_execute_grouped(const tsmm_group_item *items, int count,
-                                            tsmm_stream_t stream) {
+tsmm_status tsmm::execute_grouped(const tsmm_group_item *items, int count, tsmm_stream_t stream,
+                                  bool persistent) {
     if (count < 0 || (count > 0 && !items)) return TSMM_ERR_INVALID_ARG;
     std::set<tsmm_plan_t> seen;
     for (int i = 0; i < count; ++i) {
@@ -146,10 +146,15 @@ extern "C" tsmm_status tsmm_execute_grouped(const tsmm_group_item *items, int co
                 num_sms = p->num_sms;
             }
             gp->total_items = total;
-            cudaError_t e = dt == TSMM_F32 ? launch_grouped_f32(np, *gp, num_sms, s)
-                                           : launch_grouped_f64(np, *gp, num_sms, s);
+            cudaError_t e = dt == TSMM_F32 ? launch_grouped_f32(np, *gp, num_sms, persistent, s)
+                                           : launch_grouped_f64(np, *gp, num_sms, persistent, s);
             if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? TSMM_ERR_OUT_OF_MEMORY : TSMM_ERR_CUDA;
         }
     }
     return TSMM_OK;
+}
+
+extern "C" tsmm_status tsmm_execute_grouped(const tsmm_group_item *items, int count,
+                                            tsmm_stream_t stream) {
+    return tsmm::execute_grouped(items, count, stream, true);
 }

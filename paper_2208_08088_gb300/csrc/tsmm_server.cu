@@ -8,11 +8,20 @@
 //   * admits them in arrival order (FIFO) while the device memory pinned by
 //     admitted, unfinished requests (A + C + split-K workspace) stays within the
 //     budget, and while a workspace slice fits in the server's arena;
-//   * launches the admitted requests as one tsmm_execute_grouped batch on a
-//     free stream as soon as one is free -- requests admitted while other
-//     batches are on the GPU form the next batch, so their work overlaps;
-//   * detects batch completion with CUDA events, records completion times and
-//     returns the batch's memory to the budget and the arena.
+//   * launches the admitted requests as a batch on a free lane as soon as one
+//     is free -- requests admitted while other batches are on the GPU form the
+//     next batch, so their work overlaps.  A batch goes out cheapest request
+//     first, as a few grouped sub-batches of growing size, each with its own
+//     completion event: a small request is done when its sub-batch is, not when
+//     the largest request launched with it is.  Each lane has three
+//     high-priority streams and one low-priority stream: the first sub-batch
+//     runs as persistent launches, one per kernel class, side by side on the
+//     high-priority streams; the rest run one block per item on the
+//     low-priority one, so that the GPU's block scheduler hands SMs to newly
+//     launched small work as items finish instead of after a whole persistent
+//     launch;
+//   * detects sub-batch completion with CUDA events, records completion times
+//     and returns the sub-batch's memory to the budget and the arena.
 // Results are deterministic: each request's plan depends only on its shape,
 // never on what else is in flight.
 #include <algorithm>
@@ -91,17 +100,27 @@ struct Req {
 struct Batch {
     std::vector<Req *> reqs;
     cudaEvent_t ev = nullptr;
-    int stream = -1;
+    int lane = -1;
 };
+
+// Sub-batches per launch: a sub-batch closes once it holds kSubBatchMinBytes and
+// at least as many bytes (A + C + workspace) as all sub-batches before it, so
+// their count grows with the log of the batch's size spread.
+constexpr int kMaxSubBatches = 6;
+constexpr size_t kSubBatchMinBytes = size_t(256) << 20;
+// Streams of a lane: kHighStreams at high priority, then one at low priority.
+constexpr int kHighStreams = 3;
+constexpr int kLaneStreams = kHighStreams + 1;
 
 }  // namespace
 
 struct tsmm_server_s {
     tsmm_server_config cfg;
     int dev = 0, sms = 0;
-    std::vector<cudaStream_t> streams;
-    std::vector<char> stream_busy;
-    std::vector<cudaEvent_t> events;  // one per stream
+    std::vector<cudaStream_t> streams;    // lane i: kLaneStreams from i * kLaneStreams (high, ..., low)
+    std::vector<int> lane_pending;        // launch units in flight per lane (busy while > 0)
+    std::vector<cudaEvent_t> events;      // all of them (grown on demand)
+    std::vector<cudaEvent_t> free_events;  // not recorded by an in-flight unit
     void *ws_base = nullptr;
     void *tk_base = nullptr;
     unsigned *status_host = nullptr;  // mapped, pinned
@@ -149,35 +168,87 @@ bool tsmm_server_s::try_admit(Req *q, double t) {
 
 void tsmm_server_s::launch(double t) {
     int s = -1;
-    for (int i = 0; i < (int)streams.size(); ++i)
-        if (!stream_busy[i]) {
+    for (int i = 0; i < (int)lane_pending.size(); ++i)
+        if (lane_pending[i] == 0) {
             s = i;
             break;
         }
     if (s < 0 || forming.empty()) return;
-    std::vector<tsmm_group_item> items(forming.size());
-    for (size_t i = 0; i < forming.size(); ++i) {
-        const tsmm_request &r = forming[i]->r;
-        items[i] = tsmm_group_item{&forming[i]->plan, r.alpha, r.A_dev, r.lda, r.pb, r.beta, r.C_dev,
-                                   r.ldc};
-        forming[i]->launch_s = t;
+    // cheapest first (stable: arrival order among equals), cut into sub-batches
+    std::vector<Req *> reqs;
+    reqs.swap(forming);
+    std::stable_sort(reqs.begin(), reqs.end(), [](const Req *x, const Req *y) { return x->bytes < y->bytes; });
+    std::vector<size_t> cuts;  // end index of each sub-batch
+    size_t before = 0, cur = 0;
+    for (size_t i = 0; i < reqs.size(); ++i) {
+        cur += reqs[i]->bytes;
+        reqs[i]->launch_s = t;
+        if ((int)cuts.size() + 1 < kMaxSubBatches && i + 1 < reqs.size() && cur >= kSubBatchMinBytes &&
+            cur >= before) {
+            cuts.push_back(i + 1);
+            before += cur;
+            cur = 0;
+        }
     }
-    Batch b;
-    b.reqs = forming;
-    b.stream = s;
-    b.ev = events[s];
-    forming.clear();
-    tsmm_status st = tsmm_execute_grouped(items.data(), (int)items.size(), streams[s]);
-    if (st == TSMM_OK && cudaEventRecord(b.ev, streams[s]) != cudaSuccess) st = TSMM_ERR_CUDA;
-    if (st != TSMM_OK) {
-        finish(b, st, now_s());
-        return;
+    cuts.push_back(reqs.size());
+    // launch units: the first sub-batch split by kernel class (one grouped launch
+    // each), spread over the lane's high-priority streams so the classes run side
+    // by side; every later sub-batch one unit on the low-priority stream
+    struct Unit {
+        std::vector<Req *> reqs;
+        cudaStream_t st;
+        bool persistent;
+    };
+    std::vector<Unit> units;
+    {
+        std::map<int, std::vector<Req *>> by_class;
+        for (size_t i = 0; i < cuts[0]; ++i) by_class[reqs[i]->plan.regime * 256 + reqs[i]->plan.np].push_back(reqs[i]);
+        int h = 0;
+        for (auto &kv : by_class)
+            units.push_back(Unit{std::move(kv.second), streams[kLaneStreams * s + (h++ % kHighStreams)], true});
+        for (size_t c = 1; c < cuts.size(); ++c)
+            units.push_back(Unit{std::vector<Req *>(reqs.begin() + cuts[c - 1], reqs.begin() + cuts[c]),
+                                 streams[kLaneStreams * s + kHighStreams], false});
     }
-    stream_busy[s] = 1;
-    inflight.push_back(std::move(b));
+    tsmm_status st = TSMM_OK;
+    for (Unit &u : units) {
+        Batch b;
+        b.reqs = std::move(u.reqs);
+        if (st == TSMM_OK) {
+            std::vector<tsmm_group_item> items(b.reqs.size());
+            for (size_t i = 0; i < b.reqs.size(); ++i) {
+                const tsmm_request &r = b.reqs[i]->r;
+                items[i] = tsmm_group_item{&b.reqs[i]->plan, r.alpha, r.A_dev, r.lda, r.pb, r.beta, r.C_dev,
+                                           r.ldc};
+            }
+            if (free_events.empty()) {
+                cudaEvent_t ev;
+                if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess) {
+                    events.push_back(ev);
+                    free_events.push_back(ev);
+                }
+            }
+            if (free_events.empty()) {
+                st = TSMM_ERR_CUDA;
+            } else {
+                b.ev = free_events.back();
+                free_events.pop_back();
+                st = execute_grouped(items.data(), (int)items.size(), u.st, u.persistent);
+                if (st == TSMM_OK && cudaEventRecord(b.ev, u.st) != cudaSuccess) st = TSMM_ERR_CUDA;
+            }
+            if (st == TSMM_OK) {
+                b.lane = s;
+                ++lane_pending[s];
+                inflight.push_back(std::move(b));
+                continue;
+            }
+        }
+        finish(b, st, now_s());  // this unit and the ones after it fail
+    }
 }
 
 void tsmm_server_s::finish(Batch &b, int status, double t) {
+    if (b.ev) free_events.push_back(b.ev);
     std::lock_guard<std::mutex> lock(mu);
     for (Req *q : b.reqs) {
         inflight_bytes -= q->bytes;
@@ -188,7 +259,7 @@ void tsmm_server_s::finish(Batch &b, int status, double t) {
         delete q;
         ++completed;
     }
-    if (b.stream >= 0) stream_busy[b.stream] = 0;
+    if (b.lane >= 0) --lane_pending[b.lane];
     cv_done.notify_all();
 }
 
@@ -271,12 +342,16 @@ tsmm_status tsmm_server_create(const tsmm_server_config *cfg, tsmm_server_t *out
         *s->status_host = 0u;
         e = cudaHostGetDevicePointer(reinterpret_cast<void **>(&s->status_dev), s->status_host, 0);
     }
+    int prio_low = 0, prio_high = 0;
+    if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high);
     for (int i = 0; e == cudaSuccess && i < cfg->num_streams; ++i) {
-        cudaStream_t st;
-        cudaEvent_t ev;
-        e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
-        if (e == cudaSuccess) {
-            s->streams.push_back(st);
+        for (int h = 0; e == cudaSuccess && h < kLaneStreams; ++h) {
+            cudaStream_t st;
+            e = cudaStreamCreateWithPriority(&st, cudaStreamNonBlocking, h < kHighStreams ? prio_high : prio_low);
+            if (e == cudaSuccess) s->streams.push_back(st);
+        }
+        for (int j = 0; e == cudaSuccess && j < kMaxSubBatches; ++j) {
+            cudaEvent_t ev;
             e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
             if (e == cudaSuccess) s->events.push_back(ev);
         }
@@ -291,7 +366,8 @@ tsmm_status tsmm_server_create(const tsmm_server_config *cfg, tsmm_server_t *out
         delete s;
         return e == cudaErrorMemoryAllocation ? TSMM_ERR_OUT_OF_MEMORY : TSMM_ERR_CUDA;
     }
-    s->stream_busy.assign(s->streams.size(), 0);
+    s->lane_pending.assign(cfg->num_streams, 0);
+    s->free_events = s->events;
     s->ws_arena.init(s->cfg.arena_bytes);
     s->tk_arena.init(tk_bytes);
     s->th = std::thread([s] { s->run(); });

@@ -456,12 +456,10 @@ __global__ void __launch_bounds__(320, 1)
 template <int NP>
 static cudaError_t launch_x3_t(const CUtensorMap *tmap, const TallArgs &a, int num_sms, cudaStream_t s) {
     using Cfg = X3Cfg<NP>;
-    static bool attr_done = false;
-    if (!attr_done) {
-        cudaError_t e = cudaFuncSetAttribute(tall_bf16x3_kernel<NP>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
+    {
+        const cudaError_t e =
+            ensure_smem_limit(reinterpret_cast<const void *>(tall_bf16x3_kernel<NP>), Cfg::SMEM);
         if (e != cudaSuccess) return e;
-        attr_done = true;
     }
     const int64_t items = a.slabs * a.splits;
     const int64_t slots = num_sms > 0 ? num_sms : 1;
@@ -998,12 +996,10 @@ template <int KC>
 static cudaError_t launch_rx3_t(const CUtensorMap *tmA, const CUtensorMap *tmC, const RankArgs &a,
                                 unsigned *status, cudaStream_t s) {
     using Cfg = RX3Cfg<KC>;
-    static bool attr_done = false;
-    if (!attr_done) {
-        cudaError_t e = cudaFuncSetAttribute(rankk_bf16x3_kernel<KC>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
+    {
+        const cudaError_t e =
+            ensure_smem_limit(reinterpret_cast<const void *>(rankk_bf16x3_kernel<KC>), Cfg::SMEM);
         if (e != cudaSuccess) return e;
-        attr_done = true;
     }
     const int64_t mtiles = (a.m + kBM - 1) / kBM;
     const int64_t ntiles = (a.n + Cfg::NT - 1) / Cfg::NT;

@@ -178,12 +178,10 @@ __global__ void __launch_bounds__(TallCfg<T, NP>::THREADS, GroupCfg<T, NP>::RESI
 template <typename T, int NP>
 cudaError_t launch_grouped_t(const GroupParams &gp, int num_sms, bool persistent, cudaStream_t s) {
     using GC = GroupCfg<T, NP>;
-    static bool attr_done = false;
-    if (!attr_done) {
-        cudaError_t e = cudaFuncSetAttribute(tall_grouped_kernel<T, NP>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, GC::SMEM);
+    {
+        const cudaError_t e =
+            ensure_smem_limit(reinterpret_cast<const void *>(tall_grouped_kernel<T, NP>), GC::SMEM);
         if (e != cudaSuccess) return e;
-        attr_done = true;
     }
     const int64_t slots = persistent ? (int64_t)GC::RESIDENT * (num_sms > 0 ? num_sms : 1) : INT_MAX;
     const unsigned grid = (unsigned)(gp.total_items < slots ? gp.total_items : slots);

@@ -5,6 +5,9 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <mutex>
+#include <set>
+#include <utility>
 
 #include "../../include/tsmm.h"
 
@@ -54,6 +57,21 @@ inline int regime_of(int64_t k, int64_t n) {
 }
 
 inline int64_t round_up(int64_t x, int64_t g) { return (x + g - 1) / g * g; }
+
+// Raises a kernel's dynamic shared-memory limit to `bytes` once per (kernel,
+// device); thread-safe (the server thread and callers' threads launch alike).
+inline cudaError_t ensure_smem_limit(const void *kernel, int bytes) {
+    static std::mutex mu;
+    static std::set<std::pair<const void *, int>> done;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    if (done.count({kernel, dev})) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) done.insert({kernel, dev});
+    return e;
+}
 
 }  // namespace tsmm
 

@@ -703,12 +703,10 @@ template <bool TMA_EPI, int KC>
 static cudaError_t launch_rankk_wide_t(const CUtensorMap *tmA, const CUtensorMap *tmC, const RankArgs &a,
                                        bool vec_c, unsigned *status, cudaStream_t s) {
     using W = WideCfg<TMA_EPI, KC>;
-    static bool attr_done = false;
-    if (!attr_done) {
-        cudaError_t e = cudaFuncSetAttribute(rankk_wide_kernel<TMA_EPI, KC>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, W::SMEM);
+    {
+        const cudaError_t e =
+            ensure_smem_limit(reinterpret_cast<const void *>(rankk_wide_kernel<TMA_EPI, KC>), W::SMEM);
         if (e != cudaSuccess) return e;
-        attr_done = true;
     }
     const int64_t tiles = ((a.m + W::BMT - 1) / W::BMT) * ((a.n + W::BNT - 1) / W::BNT);
     const int64_t slots = W::RESIDENT * (int64_t)(a.num_sms > 0 ? a.num_sms : 1);
@@ -723,12 +721,10 @@ static cudaError_t launch_rankk_tma_t(const CUtensorMap *tmA, const CUtensorMap 
                                       cudaStream_t s) {
     using Cfg = RankCfg<T>;
     using TC = RankTmaCfg<T, STAGES, PF>;
-    static bool attr_done = false;
-    if (!attr_done) {
-        cudaError_t e = cudaFuncSetAttribute(rankk_tma_kernel<T, STAGES, PF>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, TC::SMEM);
+    {
+        const cudaError_t e =
+            ensure_smem_limit(reinterpret_cast<const void *>(rankk_tma_kernel<T, STAGES, PF>), TC::SMEM);
         if (e != cudaSuccess) return e;
-        attr_done = true;
     }
     const int64_t tiles = ((a.m + Cfg::BMT - 1) / Cfg::BMT) * ((a.n + Cfg::BNT - 1) / Cfg::BNT);
     const int64_t slots = (int64_t)TC::RESIDENT * (a.num_sms > 0 ? a.num_sms : 1);

@@ -453,12 +453,10 @@ __global__ void __launch_bounds__(TallCfg<T, NP>::CONSUMERS, 2)
 template <typename T, int NP>
 cudaError_t launch_tall_tma_t(const CUtensorMap *tmap, const TallArgs &a, cudaStream_t s) {
     using Cfg = TallCfg<T, NP>;
-    static bool attr_done = false;  // per instantiation; benign if raced (idempotent)
-    if (!attr_done) {
-        cudaError_t e = cudaFuncSetAttribute(tall_tma_kernel<T, NP>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
+    {
+        const cudaError_t e =
+            ensure_smem_limit(reinterpret_cast<const void *>(tall_tma_kernel<T, NP>), Cfg::SMEM);
         if (e != cudaSuccess) return e;
-        attr_done = true;
     }
     dim3 grid((unsigned)a.slabs, (unsigned)a.splits);
     tall_tma_kernel<T, NP><<<grid, Cfg::THREADS, Cfg::SMEM, s>>>(*tmap, a);
@@ -469,12 +467,10 @@ template <typename T, int NP>
 cudaError_t launch_tall_generic_t(const TallArgs &a, cudaStream_t s) {
     using Cfg = TallCfg<T, NP>;
     const int smem = Cfg::RED * (int)sizeof(T) + 16;
-    static bool attr_done = false;
-    if (!attr_done) {
-        cudaError_t e = cudaFuncSetAttribute(tall_generic_kernel<T, NP>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    {
+        const cudaError_t e =
+            ensure_smem_limit(reinterpret_cast<const void *>(tall_generic_kernel<T, NP>), smem);
         if (e != cudaSuccess) return e;
-        attr_done = true;
     }
     dim3 grid((unsigned)a.slabs, (unsigned)a.splits);
     tall_generic_kernel<T, NP><<<grid, Cfg::CONSUMERS, smem, s>>>(a);

@@ -299,9 +299,10 @@ TSMM_API int64_t tsmm_plan_cache_size(void);
  * stays within budget_bytes, and launches every group of admitted requests on
  * one of num_streams lanes as soon as a lane is free: requests admitted while
  * earlier batches run form the next batch and overlap with them on the device.
- * A batch runs cheapest request first, as up to six grouped sub-batches of
- * growing size with one completion event each (CUDA events), so a small
- * request completes with its sub-batch rather than with the whole batch.  A
+ * A batch runs cheapest request first, as up to six grouped sub-batches with
+ * one completion event each (CUDA events): a new sub-batch starts at a request
+ * that alone holds at least the bytes of the current one (and 256 MiB), so a
+ * small request completes with its sub-batch, not with a much larger request.  A
  * lane is three high-priority streams and one low-priority stream: the first
  * sub-batch runs as persistent grouped launches, one per kernel class, spread
  * over the high-priority streams; the others run one thread block per work
@@ -309,7 +310,10 @@ TSMM_API int64_t tsmm_plan_cache_size(void);
  * items finish.
  * Each request's plan depends only on its shape, so its result is the same bit
  * for bit alone or in any mix.  The caller owns A, C and the packed B, and must
- * keep them alive until the request's completion has been polled.
+ * keep them alive until the request's completion has been polled.  The
+ * server's streams are not ordered after the caller's: A, C0 and the packed B
+ * must be in place on the device (the caller's streams synchronized) before
+ * the request's arrival time.
  */
 typedef struct tsmm_server_s *tsmm_server_t;
 

@@ -103,9 +103,11 @@ struct Batch {
     int lane = -1;
 };
 
-// Sub-batches per launch: a sub-batch closes once it holds kSubBatchMinBytes and
-// at least as many bytes (A + C + workspace) as all sub-batches before it, so
-// their count grows with the log of the batch's size spread.
+// Sub-batches per launch (requests in ascending order of bytes, A + C +
+// workspace): a new sub-batch starts at a request that alone holds at least as
+// many bytes as the current sub-batch and at least kSubBatchMinBytes, so no
+// request waits for one much larger than its whole sub-batch, and their count
+// grows with the log of the batch's size spread (at most kMaxSubBatches).
 constexpr int kMaxSubBatches = 6;
 constexpr size_t kSubBatchMinBytes = size_t(256) << 20;
 // Streams of a lane: kHighStreams at high priority, then one at low priority.
@@ -179,16 +181,15 @@ void tsmm_server_s::launch(double t) {
     reqs.swap(forming);
     std::stable_sort(reqs.begin(), reqs.end(), [](const Req *x, const Req *y) { return x->bytes < y->bytes; });
     std::vector<size_t> cuts;  // end index of each sub-batch
-    size_t before = 0, cur = 0;
+    size_t cur = 0;
     for (size_t i = 0; i < reqs.size(); ++i) {
-        cur += reqs[i]->bytes;
-        reqs[i]->launch_s = t;
-        if ((int)cuts.size() + 1 < kMaxSubBatches && i + 1 < reqs.size() && cur >= kSubBatchMinBytes &&
-            cur >= before) {
-            cuts.push_back(i + 1);
-            before += cur;
+        const size_t b = reqs[i]->bytes;
+        if (cur > 0 && (int)cuts.size() + 1 < kMaxSubBatches && b >= cur && b >= kSubBatchMinBytes) {
+            cuts.push_back(i);
             cur = 0;
         }
+        cur += b;
+        reqs[i]->launch_s = t;
     }
     cuts.push_back(reqs.size());
     // launch units: the first sub-batch split by kernel class (one grouped launch

@@ -48,6 +48,8 @@ def run(server, bs, reqs, spread_s=0.0, seed=0):
         devs[q["id"]] = (dA, dC)
         batch.append((q["id"], pb, q["m"], q["alpha"], dA, q["beta"], dC,
                       t0 + (rng.uniform(0, spread_s) if spread_s else 0.0)))
+    # the server's streams are not ordered after torch's: inputs must be in place
+    torch.cuda.synchronize()
     server.submit(batch)
     server.drain(120.0)
     comps = {c["id"]: c for c in server.poll()}
@@ -116,3 +118,39 @@ def test_serving_rejects_requests_larger_than_budget():
     Cs = to_device(np.zeros((10, n), np.float32, order="F"))
     srv.submit([(1, pb, 10, 1.0, small, 0.0, Cs, tsmm.tsmm_server_clock() + 3600.0)])
     srv.close()
+
+
+def test_serving_small_requests_finish_before_a_large_one_of_their_batch():
+    """A batch goes out cheapest request first in sub-batches with their own
+    completion events: small requests launched with a large one complete
+    before it, with correct results."""
+    bs = make_bs()
+    k_s, n_s, B_s, pb_s = bs[5]
+    m_big, k_big, n_big = 131072, 4096, 64
+    A_big = torch.empty((k_big, m_big), dtype=torch.float32, device="cuda")
+    ti.fill_torch(A_big, 7, "uniform")
+    A_big = A_big.t()
+    B_big = torch.empty((n_big, k_big), dtype=torch.float32, device="cuda")
+    ti.fill_torch(B_big, 8, "uniform")
+    pb_big = tsmm.pack_b(B_big.t())
+    C_big = torch.zeros((n_big, m_big), dtype=torch.float32, device="cuda").t()
+    smalls = []
+    for rid in range(1, 17):
+        A = ti.matrix_np(1024, k_s, 3000 + rid, "uniform", np.float32)
+        smalls.append((rid, A, to_device(A), to_device(np.zeros((1024, n_s), np.float32, order="F"))))
+    torch.cuda.synchronize()  # inputs in place before the server's streams read them
+    srv = tsmm.Server(budget_bytes=40 << 30, num_streams=1, max_batch=64)
+    t0 = tsmm.tsmm_server_clock() + 0.005
+    batch = [(0, pb_big, m_big, 1.0, A_big, 0.0, C_big, t0)]
+    batch += [(rid, pb_s, 1024, 1.0, dA, 0.0, dC, t0) for (rid, A, dA, dC) in smalls]
+    srv.submit(batch)
+    srv.drain(120.0)
+    comps = {c["id"]: c for c in srv.poll()}
+    srv.close()
+    assert len(comps) == 17 and all(c["status"] == 0 for c in comps.values())
+    assert len({c["launch_s"] for c in comps.values()}) == 1, "expected one batch"
+    assert max(comps[rid]["complete_s"] for rid in range(1, 17)) < comps[0]["complete_s"]
+    for (rid, A, dA, dC) in smalls:
+        Cref, E = oracle.tsmm(1.0, A, B_s, 0.0, None)
+        ok, ratio, nbad = oracle.check(dC.cpu().numpy(), Cref, E, np.float32)
+        assert ok, f"request {rid}: {nbad} entries outside the bound"

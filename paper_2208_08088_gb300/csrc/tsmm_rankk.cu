@@ -18,6 +18,8 @@
 // start, so the C0 read overlaps the A/B traffic and the products; otherwise
 // the epilogue loads C0 in batches ahead of its stores.  A plain-load kernel
 // covers unaligned A.
+#include <type_traits>
+
 #include "tsmm_device.cuh"
 #include "tsmm_internal.h"
 
@@ -72,6 +74,15 @@ struct RankAcc {
         }
     }
     __device__ __forceinline__ T get(int r, int c) const { return v[r][c]; }
+    // start from C0 given in the epilogue's layout (c0v[c][rg].v[r] is row rg*VEC + r)
+    __device__ __forceinline__ void init(const Vec<T, Cfg::VEC> (&c0v)[4][2]) {
+#pragma unroll
+        for (int c = 0; c < Cfg::TN; ++c)
+#pragma unroll
+            for (int rg = 0; rg < 2; ++rg)
+#pragma unroll
+                for (int r = 0; r < Cfg::VEC; ++r) v[rg * Cfg::VEC + r][c] = c0v[c][rg].v[r];
+    }
 };
 
 template <>
@@ -102,6 +113,15 @@ struct RankAcc<float> {
     }
     __device__ __forceinline__ float get(int r, int c) const {
         return (r & 1) ? v[r / 2][c].y : v[r / 2][c].x;
+    }
+    __device__ __forceinline__ void init(const Vec<float, Cfg::VEC> (&c0v)[4][2]) {
+#pragma unroll
+        for (int c = 0; c < Cfg::TN; ++c)
+#pragma unroll
+            for (int rg = 0; rg < 2; ++rg)
+#pragma unroll
+                for (int r = 0; r < Cfg::VEC; r += 2)
+                    v[(rg * Cfg::VEC + r) / 2][c] = make_float2(c0v[c][rg].v[r], c0v[c][rg].v[r + 1]);
     }
 };
 
@@ -203,7 +223,7 @@ struct RankTmaCfg {
 // producer warp runs ahead of the consumers by up to STAGES k-chunks and, with
 // PREFETCH_C0, by one C0 tile, so the next tile's loads overlap this tile's
 // products and stores.
-template <typename T, int STAGES, bool PREFETCH_C0>
+template <typename T, int STAGES, bool PREFETCH_C0, bool C0_INIT = false>
 __global__ void __launch_bounds__(RankCfg<T>::CONSUMERS + 32, 2)
     rankk_tma_kernel(const __grid_constant__ CUtensorMap tmA,
                      const __grid_constant__ CUtensorMap tmC, const RankArgs a, bool vec_c,
@@ -289,6 +309,11 @@ __global__ void __launch_bounds__(RankCfg<T>::CONSUMERS + 32, 2)
     const int tn = tid / 16;
     const T ealpha = static_cast<T>(a.alpha);  // converted once, not per tile
     const T ebeta = static_cast<T>(a.beta);
+    // C0_INIT (FP64, alpha = beta = 1, C0 prefetched a tile ahead): the
+    // accumulators start from C0, so the epilogue has no arithmetic left -- at
+    // small k the k fmas per output and the epilogue's one share the FP64 pipe.
+    // The sum is C0 + a1*b1 + ... in fma order: another order of the same terms.
+    static_assert(!C0_INIT || PREFETCH_C0, "C0 comes from the prefetched tile");
     int64_t g = 0;
     int j = 0;
     for (int64_t t = blockIdx.x; t < ntiles_total; t += gridDim.x, ++j) {
@@ -296,8 +321,21 @@ __global__ void __launch_bounds__(RankCfg<T>::CONSUMERS + 32, 2)
         udivmod(t, mtiles, tile, mt);
         const int64_t i0 = mt * Cfg::BMT;
         RankAcc<T> acc;
-        acc.zero();
         bool ok = true;
+        if constexpr (C0_INIT) {
+            const int b = j % 2;
+            if (!mbar_wait_bounded(&cfull[b], (j / 2) & 1)) {
+                if (lane == 0) atomicOr(status, kDevErrTimeout);
+                return;  // this warp's part of the tile is not written; the host sees TSMM_ERR_TIMEOUT
+            }
+            RankEpilogue<T> e0;
+            e0.load(a, i0, tile, tm, tn, vec_c, sC + b * Cfg::C_TILE, ebeta);
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&cempty[b]);  // C0 buffer b may be refilled
+            acc.init(e0.c0v);
+        } else {
+            acc.zero();
+        }
         for (int c = 0; c < nchunks; ++c, ++g) {
             const int st = (int)(g % STAGES);
             if (!mbar_wait_bounded(&full[st], (int)((g / STAGES) & 1))) {
@@ -310,6 +348,14 @@ __global__ void __launch_bounds__(RankCfg<T>::CONSUMERS + 32, 2)
             acc.chunk(sA, sA + Cfg::A_CHUNK, kcnt, tm, tn);
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty[st]);
+        }
+        if constexpr (C0_INIT) {
+            if (!ok) {
+                if (lane == 0) atomicOr(status, kDevErrTimeout);
+                return;
+            }
+            RankEpilogue<T>().store(acc, a, i0, tile, tm, tn, vec_c, T(1), T(0));  // C0 is in acc
+            continue;
         }
         RankEpilogue<T> ep;
         const int b = j % 2;
@@ -715,21 +761,21 @@ static cudaError_t launch_rankk_wide_t(const CUtensorMap *tmA, const CUtensorMap
     return cudaGetLastError();
 }
 
-template <typename T, int STAGES, bool PF>
+template <typename T, int STAGES, bool PF, bool C0I = false>
 static cudaError_t launch_rankk_tma_t(const CUtensorMap *tmA, const CUtensorMap *tmC,
                                       const RankArgs &a, bool vec_c, unsigned *status,
                                       cudaStream_t s) {
     using Cfg = RankCfg<T>;
     using TC = RankTmaCfg<T, STAGES, PF>;
     {
-        const cudaError_t e =
-            ensure_smem_limit(reinterpret_cast<const void *>(rankk_tma_kernel<T, STAGES, PF>), TC::SMEM);
+        const cudaError_t e = ensure_smem_limit(
+            reinterpret_cast<const void *>(rankk_tma_kernel<T, STAGES, PF, C0I>), TC::SMEM);
         if (e != cudaSuccess) return e;
     }
     const int64_t tiles = ((a.m + Cfg::BMT - 1) / Cfg::BMT) * ((a.n + Cfg::BNT - 1) / Cfg::BNT);
     const int64_t slots = (int64_t)TC::RESIDENT * (a.num_sms > 0 ? a.num_sms : 1);
     const unsigned grid = (unsigned)(tiles < slots ? tiles : slots);
-    rankk_tma_kernel<T, STAGES, PF><<<grid, TC::THREADS, TC::SMEM, s>>>(*tmA, *tmC, a, vec_c, status);
+    rankk_tma_kernel<T, STAGES, PF, C0I><<<grid, TC::THREADS, TC::SMEM, s>>>(*tmA, *tmC, a, vec_c, status);
     return cudaGetLastError();
 }
 
@@ -753,7 +799,12 @@ static cudaError_t launch_rankk_t(const CUtensorMap *tmA, const CUtensorMap *tmC
         }
         // output-bound shapes: one k chunk, C0 prefetched by TMA when it is read
         if (a.k <= Cfg::KC) {
-            if (tmC && a.beta != 0.0) return launch_rankk_tma_t<T, 1, true>(tmA, tmC, a, vec_c, status, s);
+            if (tmC && a.beta != 0.0) {
+                if constexpr (std::is_same<T, double>::value)
+                    if (a.alpha == 1.0 && a.beta == 1.0)
+                        return launch_rankk_tma_t<T, 1, true, true>(tmA, tmC, a, vec_c, status, s);
+                return launch_rankk_tma_t<T, 1, true>(tmA, tmC, a, vec_c, status, s);
+            }
             return launch_rankk_tma_t<T, 1, false>(tmA, tmA, a, vec_c, status, s);
         }
         return launch_rankk_tma_t<T, 2, false>(tmA, tmA, a, vec_c, status, s);

@@ -268,6 +268,18 @@ def test_rankk_persistent_many_tiles(dtype, k, beta, m):
     assert_parity(C, A, B, C0 if beta != 0 else None, 1.0 if k != 33 else 0.75, beta)
 
 
+@pytest.mark.parametrize("k", [1, 8, 32])
+def test_rankk_f64_alpha_beta_one_integer_exact(k):
+    """FP64 with alpha = beta = 1 and k within one chunk starts its
+    accumulators from C0 (another summation order of the same terms): exact on
+    integers, over several tiles per block."""
+    m, n = 2048, 1000
+    A, B, C0 = gen(m, n, k, np.float64, "integer")
+    C, pl, _ = run(A, B, C0, 1.0, 1.0)
+    assert pl.info()["regime"] == 2
+    assert_parity(C, A, B, C0, 1.0, 1.0, exact=True)
+
+
 def test_config1_integer_matches_golden_fixture():
     """GPU rows of the m = k = 2048, n = 16 integer workload equal the committed
     fixture (written by tests/golden/make_golden.py from the oracle) bit for bit."""

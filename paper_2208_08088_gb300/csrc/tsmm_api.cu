@@ -341,7 +341,7 @@ tsmm_status plan_layout(int64_t m, int64_t n, int64_t k, tsmm_dtype dtype, int f
         }
     } else if (regime == 1) {
         p->np = tall_np(n);
-        p->bm = tall_bm(dtype);
+        p->bm = tall_bm(dtype, p->np);
         p->kp = round_up(k, kTallBKS);
         p->slabs = (m + p->bm - 1) / p->bm;
         const int64_t kstages = p->kp / kTallBKS;

@@ -42,8 +42,13 @@ inline int tall_np(int64_t n) {
     return pow2_ceil(n);
 }
 
-// Rows per thread block of the regime-(i) kernel (see tall kernel header).
-inline int tall_bm(tsmm_dtype d) { return d == TSMM_F64 ? 64 : 128; }
+// Rows per thread block (m-slab) of the regime-(i) kernel: FP32 n = 25..32
+// takes 256 rows, so that its four consumer warps (64 rows each with 8 x 8
+// thread tiles) split the slab by rows and each reads whole 32-column stages,
+// instead of two warps splitting every stage's k columns (one stage wait per
+// 16 k-steps).  Other FP32 widths 128, FP64 64.
+constexpr int tall_block_rows(bool f64, int np) { return f64 ? 64 : (np == 32 ? 256 : 128); }
+inline int tall_bm(tsmm_dtype d, int np) { return tall_block_rows(d == TSMM_F64, np); }
 
 // Thread blocks of the regime-(i) TMA kernel resident per SM (its shared-memory
 // ring is sized for this): 3 for the FMA-bound FP32 shapes (n >= 32), else 2.

@@ -79,7 +79,7 @@ extern "C" tsmm_status tsmm_execute_noalloc(tsmm_dtype dtype, int64_t m, int64_t
     if (n > kTallMaxN) return TSMM_ERR_UNSUPPORTED_SHAPE;
     const size_t es = dtype_size(dtype);
     const int np = tall_np(n);
-    const int bm = tall_bm(dtype);
+    const int bm = tall_bm(dtype, np);
     const int64_t kp = round_up(k, kTallBKS);
     const int64_t slabs = (m + bm - 1) / bm;
     // scratch layout: [error word][arrival counters][packed B][split-K partials]

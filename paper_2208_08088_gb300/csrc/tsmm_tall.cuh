@@ -51,7 +51,7 @@ struct TallCfg {
     static constexpr int GSTRIDE = WROWS / RG;         // distance between a thread's groups
     // local row of this thread's row r, given rloc = wm*WROWS + lr*RV
     static __host__ __device__ constexpr int row(int rloc, int r) { return rloc + (r / RV) * GSTRIDE + r % RV; }
-    static constexpr int BM = (sizeof(T) == 4) ? 128 : 64;
+    static constexpr int BM = tall_block_rows(sizeof(T) == 8, NP);
     static constexpr int WM = BM / WROWS;              // warps along m
     static constexpr int NWARPS = kTallConsumerWarps;
     static constexpr int WK = NWARPS / WM;             // warps along k

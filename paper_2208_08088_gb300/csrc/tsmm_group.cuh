@@ -37,7 +37,7 @@ struct GroupCfg {
     static constexpr int RED_BYTES = Tc::RED * (int)sizeof(T);
     // three blocks per SM where two ring stages and the reduction buffer fit in
     // a third of the SM's shared memory (the FMA-bound FP32 width 48: more warps
-    // to hide shared-memory latency; width 32's 256-row stages do not fit),
+    // to hide shared-memory latency; the 256-row stages of width 32 do not fit),
     // else two with a deeper ring
     static constexpr bool THREE = sizeof(T) == 4 && (NP == 32 || NP == 48) &&
                                   2 * Tc::STAGE_BYTES + RED_BYTES <= 72 * 1024;

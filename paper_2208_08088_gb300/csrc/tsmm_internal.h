@@ -42,14 +42,15 @@ inline int tall_np(int64_t n) {
     return pow2_ceil(n);
 }
 
-// Rows per thread block (m-slab) of the regime-(i) kernel: FP32 widths 24 and
-// 32 take 256 rows, so that their four consumer warps (64 rows each: 4 x 12
-// and 8 x 8 thread tiles) split the slab by rows and each reads whole
-// 32-column stages, instead of two warps splitting every stage's k columns (one
-// stage wait per 16 k-steps; n = 24: 0.83 -> 0.79 ms, n = 32: 1.01 -> 0.98 ms
-// at m = k = 32768).  Other FP32 widths 128, FP64 64.
+// Rows per thread block (m-slab) of the regime-(i) kernel.  FP32 widths up to
+// 32 take 256 rows: the consumer warps then split the slab by rows more and the
+// stage's k columns less (widths 24 and 32: each warp reads whole 32-column
+// stages instead of two warps splitting every stage, one stage wait per 16
+// k-steps -- n = 24: 0.83 -> 0.79 ms, n = 32: 1.01 -> 0.98 ms at m = k = 32768;
+// widths up to 16: 4 -> 2 warps per stage, 0.5-1.5 % faster).  FP32 widths 48
+// and 64 take 128 (their warps already own whole stages), FP64 64.
 constexpr int tall_block_rows(bool f64, int np) {
-    return f64 ? 64 : ((np == 24 || np == 32) ? 256 : 128);
+    return f64 ? 64 : ((np == 48 || np == 64) ? 128 : 256);
 }
 inline int tall_bm(tsmm_dtype d, int np) { return tall_block_rows(d == TSMM_F64, np); }
 

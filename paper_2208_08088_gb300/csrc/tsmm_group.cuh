@@ -36,10 +36,9 @@ struct GroupCfg {
     using Tc = TallCfg<T, NP>;
     static constexpr int RED_BYTES = Tc::RED * (int)sizeof(T);
     // three blocks per SM where two ring stages and the reduction buffer fit in
-    // a third of the SM's shared memory (the FMA-bound FP32 width 48: more warps
-    // to hide shared-memory latency; the 256-row stages of width 32 do not fit),
-    // else two with a deeper ring
-    static constexpr bool THREE = sizeof(T) == 4 && (NP == 32 || NP == 48) &&
+    // a third of the SM's shared memory and the width's tiles fit its registers
+    // (more warps to hide shared-memory latency), else two with a deeper ring
+    static constexpr bool THREE = tall_resident_blocks(sizeof(T) == 8, NP) == 3 &&
                                   2 * Tc::STAGE_BYTES + RED_BYTES <= 72 * 1024;
     static constexpr int RESIDENT = THREE ? 3 : 2;
     static constexpr int RING_BUDGET = (THREE ? 72 : 100) * 1024 - RED_BYTES;

@@ -47,16 +47,16 @@ inline int tall_np(int64_t n) {
 // stage's k columns less (widths 24 and 32: each warp reads whole 32-column
 // stages instead of two warps splitting every stage, one stage wait per 16
 // k-steps -- n = 24: 0.83 -> 0.79 ms, n = 32: 1.01 -> 0.98 ms at m = k = 32768;
-// widths up to 16: 4 -> 2 warps per stage, 0.5-1.5 % faster).  FP32 widths 48
-// and 64 take 128 (their warps already own whole stages), FP64 64.
-constexpr int tall_block_rows(bool f64, int np) {
-    return f64 ? 64 : ((np == 48 || np == 64) ? 128 : 256);
-}
+// widths up to 16: 4 -> 2 warps per stage, 0.5-1.5 % faster; width 48 with
+// its 8 x 12 tiles likewise).  The FP32 width 64 takes 128 (its warps already
+// own whole stages), FP64 64.
+constexpr int tall_block_rows(bool f64, int np) { return f64 ? 64 : (np == 64 ? 128 : 256); }
 inline int tall_bm(tsmm_dtype d, int np) { return tall_block_rows(d == TSMM_F64, np); }
 
 // Thread blocks of the regime-(i) TMA kernel resident per SM (its shared-memory
-// ring is sized for this): 3 for the FMA-bound FP32 shapes (n >= 32), else 2.
-constexpr int tall_resident_blocks(bool f64, int np) { return (!f64 && np >= 32) ? 3 : 2; }
+// ring is sized for this): 3 for the FMA-bound FP32 widths 32 and 64 (8 x 8
+// tiles fit 136 registers), else 2 (the width 48's 8 x 12 tiles need ~160).
+constexpr int tall_resident_blocks(bool f64, int np) { return (!f64 && (np == 32 || np == 64)) ? 3 : 2; }
 
 // Regime of a (k, n) pair: 1 = tall (n <= 64), 2 = rank-k (k <= 128), 0 = unsupported.
 inline int regime_of(int64_t k, int64_t n) {

@@ -33,16 +33,19 @@ namespace tsmm {
 template <typename T, int NP>
 struct TallCfg {
     static constexpr int VEC = 16 / (int)sizeof(T);   // elements per 16-byte vector
-    // The FMA-bound FP32 shapes (n >= 32) use 8 x 8 thread tiles: 32 packed
-    // fmas per 4 shared-memory loads of 16 bytes (a 16-byte load costs four
-    // shared-memory wavefronts whatever its address pattern, and the 4 x 16
-    // tile's 5 loads per 32 fmas saturate them before the FMA pipe).  A
-    // thread's 8 rows are two groups of 4, half a warp tile apart, so the
-    // lanes along m read adjacent 16-byte words of A (no bank shared).
-    // The widths 24 and 48 use 12 columns per thread (2 or 4 lane groups).
-    static constexpr bool WIDE = sizeof(T) == 4 && (NP == 32 || NP == 64);
+    // The FMA-bound FP32 shapes (n >= 32) use 8-row thread tiles: 8 x 8 (32
+    // packed fmas per 4 shared-memory loads of 16 bytes; a 16-byte load costs
+    // four shared-memory wavefronts whatever its address pattern, and the
+    // 4 x 16 tile's 5 loads per 32 fmas saturate them before the FMA pipe), and
+    // 8 x 12 for the width 48 (5 loads per 48 packed fmas; n = 48 at
+    // m = k = 32768: 1.52 -> 1.46 ms against 4 x 12).  A thread's 8 rows are two
+    // groups of 4, half a warp tile apart, so the lanes along m read adjacent
+    // 16-byte words of A (no bank shared).  FP32 width 24 and FP64 widths 24
+    // and 48 use VEC x 12 tiles.
+    static constexpr bool WIDE = sizeof(T) == 4 && (NP == 32 || NP == 48 || NP == 64);
     static constexpr int R = WIDE ? 8 : VEC;  // rows per thread
-    static constexpr int CN = WIDE ? 8 : ((NP == 24 || NP == 48) ? 12 : (NP < 16 ? NP : 16));  // columns per thread
+    static constexpr int CN = WIDE ? (NP == 48 ? 12 : 8)
+                                   : ((NP == 24 || NP == 48) ? 12 : (NP < 16 ? NP : 16));  // columns per thread
     static constexpr int G = NP / CN;                  // lane groups along n
     static constexpr int LR = 32 / G;                  // lanes along m
     static constexpr int WROWS = LR * R;               // rows per warp

@@ -31,8 +31,11 @@ __all__ = [
     "tsmm_packed_b_info", "tsmm_packed_b_read", "tsmm_plan", "tsmm_plan_destroy", "tsmm_plan_info", "tsmm_execute",
     "tsmm_plan_check", "tsmm_plan_launches_per_execute", "tsmm_autotune",
     "tsmm_plan_cache_load", "tsmm_plan_cache_save", "tsmm_plan_cache_clear", "tsmm_plan_cache_size",
+    "tsmm_execute_noalloc", "tsmm_last_cuda_error", "tsmm_diag_bounded_wait", "diag_bounded_wait",
     "autotune", "execute_grouped", "tsmm_execute_grouped", "GroupItem",
     "Server", "ServerConfig", "Request", "Completion", "tsmm_server_clock",
+    "tsmm_server_create", "tsmm_server_submit", "tsmm_server_poll", "tsmm_server_drain",
+    "tsmm_server_destroy",
     "PackedB", "Plan", "pack_b", "plan", "execute", "colmajor", "ld_of",
 ]
 
@@ -145,6 +148,8 @@ def _load():
     L.tsmm_diag_bounded_wait.restype = ci
     L.tsmm_diag_bounded_wait.argtypes = [ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint64),
                                          ctypes.POINTER(dbl)]
+    L.tsmm_execute_noalloc.restype = ci
+    L.tsmm_execute_noalloc.argtypes = [ci, i64, i64, i64, dbl, vp, i64, vp, i64, dbl, vp, i64, vp]
     return L
 
 
@@ -254,6 +259,21 @@ def tsmm_autotune(m: int, n: int, k: int, dtype: int, A_dev: int, lda: int, pb: 
     _check(lib.tsmm_autotune(m, n, k, dtype, A_dev or None, lda, pb, C_dev or None, ldc,
                              stream or None, reps, ctypes.byref(out)), "tsmm_autotune")
     return out.value
+
+
+def tsmm_execute_noalloc(dtype: int, m: int, n: int, k: int, alpha: float, A_dev: int, lda: int,
+                         B_dev: int, ldb: int, beta: float, C_dev: int, ldc: int,
+                         stream: int = 0) -> None:
+    """Allocation-free C = alpha*A*B + beta*C0 for regime (i) shapes: B is
+    packed into the library's built-in device scratch on every call."""
+    _check(lib.tsmm_execute_noalloc(dtype, m, n, k, alpha, A_dev or None, lda, B_dev or None, ldb,
+                                    beta, C_dev or None, ldc, stream or None),
+           "tsmm_execute_noalloc")
+
+
+def tsmm_last_cuda_error() -> str:
+    """Text of the last CUDA error the library saw (empty if none)."""
+    return lib.tsmm_last_cuda_error().decode()
 
 
 def tsmm_plan_cache_load(path: str) -> None:
@@ -402,6 +422,11 @@ def execute_grouped(problems, stream=None) -> None:
     tsmm_execute_grouped(items, _stream_handle(stream))
 
 
+def tsmm_diag_bounded_wait(polls: int):
+    """Same-named form of diag_bounded_wait: (status, cycles, seconds)."""
+    return diag_bounded_wait(polls)
+
+
 def diag_bounded_wait(polls: int):
     """Run the library's bounded mbarrier wait against a barrier that nothing
     completes (tsmm_diag_bounded_wait); returns (status, cycles, seconds) --
@@ -436,6 +461,31 @@ def execute(p: Plan, alpha: float, A, pb: PackedB, beta: float, C, stream=None) 
 # ------------------------------------------------------------------ serving
 def tsmm_server_clock() -> float:
     return float(lib.tsmm_server_clock())
+
+
+def tsmm_server_create(cfg: "ServerConfig") -> int:
+    """A tsmm_server_t handle (as an int) for the given ServerConfig."""
+    out = ctypes.c_void_p()
+    _check(lib.tsmm_server_create(ctypes.byref(cfg), ctypes.byref(out)), "tsmm_server_create")
+    return out.value
+
+
+def tsmm_server_submit(server: int, reqs, count: int) -> None:
+    """Submit `count` entries of a ctypes array of Request."""
+    _check(lib.tsmm_server_submit(server, reqs, count), "tsmm_server_submit")
+
+
+def tsmm_server_poll(server: int, out, max_items: int) -> int:
+    """Fill a ctypes array of Completion; returns how many were written."""
+    return int(lib.tsmm_server_poll(server, out, max_items))
+
+
+def tsmm_server_drain(server: int, timeout_s: float) -> None:
+    _check(lib.tsmm_server_drain(server, timeout_s), "tsmm_server_drain")
+
+
+def tsmm_server_destroy(server: int) -> None:
+    _check(lib.tsmm_server_destroy(server), "tsmm_server_destroy")
 
 
 class Server:

@@ -104,3 +104,23 @@ def test_plan_cache_file_roundtrip(tmp_path):
 
 def test_last_cuda_error_string():
     assert isinstance(tsmm.lib.tsmm_last_cuda_error().decode(), str)
+
+
+def test_binding_has_every_entry_point_under_its_c_name():
+    """The Python binding is the C ABI under the same names (marshalling only)."""
+    missing = [s for s in declared_symbols() if not callable(getattr(tsmm, s, None))]
+    assert not missing, missing
+
+
+def test_noalloc_argument_errors_before_device_work():
+    with pytest.raises(tsmm.TsmmError) as e:
+        tsmm.tsmm_execute_noalloc(tsmm.F32, -1, 4, 4, 1.0, 0, 1, 0, 4, 0.0, 0, 1)
+    assert e.value.status == 1
+    with pytest.raises(tsmm.TsmmError) as e:
+        tsmm.tsmm_execute_noalloc(tsmm.F32, 100, 65, 8, 1.0, 0, 100, 0, 8, 0.0, 0, 100)
+    assert e.value.status == 2
+    with pytest.raises(tsmm.TsmmError) as e:
+        tsmm.tsmm_execute_noalloc(tsmm.F32, 100, 8, 8, 1.0, 0, 99, 0, 8, 0.0, 0, 100)
+    assert e.value.status == 1
+    # m = 0 or n = 0: nothing to do, no device touched
+    tsmm.tsmm_execute_noalloc(tsmm.F32, 0, 8, 8, 1.0, 0, 1, 0, 8, 0.0, 0, 1)

@@ -36,9 +36,10 @@ def test_config1_2048x2048x16(dist, dtype):
 
 # ------------------------------------------------------------- regime (i) sweep
 @pytest.mark.parametrize("dtype", DT)
-@pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 8, 9, 16, 17, 31, 32, 33, 48, 63, 64])
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 8, 9, 16, 17, 20, 24, 31, 32, 33, 40, 48, 63, 64])
 def test_tall_all_n_ragged(dtype, n):
-    """m, k not multiples of the tile sizes (128/64 rows, 32-column stages)."""
+    """m, k not multiples of the tile sizes (256/128/64-row slabs, 32-column
+    stages), every padded width (1, 2, 4, 8, 16, 24, 32, 48, 64)."""
     m, k = 1000, 777
     A, B, C0 = gen(m, n, k, dtype)
     C, pl, _ = run(A, B, C0, -1.25, 0.75)
@@ -56,7 +57,7 @@ def test_tall_small_and_edges(dtype, m, n, k):
 
 
 @pytest.mark.parametrize("dtype", DT)
-@pytest.mark.parametrize("n", [1, 16, 64])
+@pytest.mark.parametrize("n", [1, 16, 24, 32, 48, 64])
 def test_tall_split_k_integer_exact(dtype, n):
     """Few m-slabs and long k force split-K (S > 1); integer inputs make the
     result independent of the summation order, so it must be bit-exact."""

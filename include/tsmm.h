@@ -381,7 +381,8 @@ TSMM_API double tsmm_server_clock(void);
  * the library holds until the process exits.  The k split is reduced so the
  * partial tiles fit; sizes whose packed B (k rounded up to 32, times n rounded
  * up to one of 1, 2, 4, 8, 16, 24, 32, 48, 64, times the element size) plus one arrival counter per
- * 128 (F32) / 64 (F64) rows of m do not fit return TSMM_ERR_UNSUPPORTED_SHAPE
+ * m-slab (256 rows for F32 with n <= 48, 128 for F32 with n > 48, 64 for F64; the plan's bm)
+ * do not fit return TSMM_ERR_UNSUPPORTED_SHAPE
  * before any device work, as do shapes with n > 64.
  *
  * The first call on each device looks up the array's device address

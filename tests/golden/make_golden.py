@@ -3,7 +3,7 @@
 
     python tests/golden/make_golden.py
 
-config1_integer_rows.json: the m = k = 2048, n = 16 workload (alpha = 1.5,
+tsmm_2048x2048x16_integer_rows.json: the m = k = 2048, n = 16 workload (alpha = 1.5,
 beta = 0.5) with integer-valued inputs in [-4, 4] (seeds A = 1, B = 2, C0 = 3):
 every partial sum is an integer below 2^15, so C is exact in FP32 and the
 stored rows are the unique correct result for any summation order.
@@ -23,7 +23,7 @@ import tsmm_inputs as ti  # noqa: E402
 ROWS = [0, 1, 2, 127, 128, 1000, 1023, 1024, 2046, 2047]
 
 
-def config1_integer():
+def integer_2048x2048x16():
     m = k = 2048
     n = 16
     A = np.asfortranarray(ti.rows_np(ROWS, m, k, ti.SEED_A, "integer", np.float32))
@@ -37,8 +37,8 @@ def config1_integer():
 
 
 def main():
-    with open(os.path.join(HERE, "config1_integer_rows.json"), "w") as f:
-        json.dump(config1_integer(), f, indent=1)
+    with open(os.path.join(HERE, "tsmm_2048x2048x16_integer_rows.json"), "w") as f:
+        json.dump(integer_2048x2048x16(), f, indent=1)
 
 
 if __name__ == "__main__":

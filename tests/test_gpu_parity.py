@@ -24,10 +24,10 @@ def gen(m, n, k, dtype, dist="uniform", seeds=(ti.SEED_A, ti.SEED_B, ti.SEED_C0)
             ti.matrix_np(m, n, seeds[2], dist, dtype))
 
 
-# ------------------------------------------------------------- BASELINE config 1
+# ------------------------------------------------------------- m = k = 2048, n = 16, alpha = 1.5, beta = 0.5
 @pytest.mark.parametrize("dist", ["uniform", "integer"])
 @pytest.mark.parametrize("dtype", DT)
-def test_config1_2048x2048x16(dist, dtype):
+def test_2048x2048x16_alpha_beta(dist, dtype):
     """m = k = 2048, n = 16, alpha = 1.5, beta = 0.5, B packed once."""
     A, B, C0 = gen(2048, 16, 2048, dtype, dist)
     C, pl, _ = run(A, B, C0, 1.5, 0.5)
@@ -281,13 +281,13 @@ def test_rankk_f64_alpha_beta_one_integer_exact(k):
     assert_parity(C, A, B, C0, 1.0, 1.0, exact=True)
 
 
-def test_config1_integer_matches_golden_fixture():
+def test_2048x2048x16_integer_matches_golden_fixture():
     """GPU rows of the m = k = 2048, n = 16 integer workload equal the committed
     fixture (written by tests/golden/make_golden.py from the oracle) bit for bit."""
     import json
     import os
     fx = json.load(open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
-                                     "config1_integer_rows.json")))
+                                     "tsmm_2048x2048x16_integer_rows.json")))
     m, n, k = fx["m"], fx["n"], fx["k"]
     A, B, C0 = gen(m, n, k, np.float32, "integer")
     C, _, _ = run(A, B, C0, fx["alpha"], fx["beta"])

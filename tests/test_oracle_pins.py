@@ -361,7 +361,7 @@ def test_golden_fixture_reproduces():
     spec = importlib.util.spec_from_file_location("make_golden", path)
     mg = importlib.util.module_from_spec(spec)
     spec.loader.exec_module(mg)
-    stored = json.load(open(os.path.join(root, "tests", "golden", "config1_integer_rows.json")))
-    assert mg.config1_integer() == stored
+    stored = json.load(open(os.path.join(root, "tests", "golden", "tsmm_2048x2048x16_integer_rows.json")))
+    assert mg.integer_2048x2048x16() == stored
     # and the stored values are integers / 2 (alpha = 1.5, beta = 0.5 on integers)
     assert all(float(2 * x).is_integer() for row in stored["C_rows"] for x in row)

@@ -344,15 +344,23 @@ typedef struct tsmm_completion {
     int status;                                      /* tsmm_status of the request */
 } tsmm_completion;
 
-/* Create a server on the current device (allocates its arena, streams, events). */
+/* Create a server on the current device (allocates its arena, streams, events
+   and starts its scheduler thread).  INVALID_ARG for a NULL argument, a dtype
+   other than F32/F64, budget_bytes == 0, num_streams outside 1..16 or max_batch
+   outside 1..1024; OUT_OF_MEMORY / CUDA if an allocation fails (nothing is
+   left allocated).  *out is written only on TSMM_OK; the server owns
+   everything it allocates until tsmm_server_destroy. */
 TSMM_API tsmm_status tsmm_server_create(const tsmm_server_config *cfg, tsmm_server_t *out);
 /* Queue requests (thread-safe).  INVALID_ARG for a request that could never be
    admitted (its bytes exceed the budget) or has bad arguments; none of the
    requests of a failing call is queued. */
 TSMM_API tsmm_status tsmm_server_submit(tsmm_server_t s, const tsmm_request *reqs, int count);
-/* Wait until every submitted request has completed (TIMEOUT after timeout_s seconds). */
+/* Wait until every submitted request has completed (TIMEOUT after timeout_s
+   seconds, INVALID_ARG for a NULL server).  A request whose kernels gave up
+   (a bounded wait ran out) completes with status TSMM_ERR_TIMEOUT. */
 TSMM_API tsmm_status tsmm_server_drain(tsmm_server_t s, double timeout_s);
-/* Move up to max completions into out; returns how many. */
+/* Move up to max completions into out (completion order); returns how many
+   (0 for a NULL server or out, or max <= 0). */
 TSMM_API int64_t tsmm_server_poll(tsmm_server_t s, tsmm_completion *out, int64_t max);
 /* Stop the scheduler (requests not yet admitted are dropped), wait for the
    admitted ones, free everything. */

@@ -31,3 +31,30 @@ def test_reference_arm_other_ranks_exit_quietly():
     res = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1", "--warmup", "1"],
                          cwd=ROOT, env=env, capture_output=True, text=True, timeout=120)
     assert res.returncode == 0 and res.stdout.strip() == ""
+
+
+def test_workloads_and_roofline_arithmetic():
+    """The default step is the FP32 sweep m = k = 32768, n in {1, 2, 4, 8, 16, 32,
+    64}, beta in {0, 1}; the rank-k workload is m = n = 16384, k in {4..128},
+    beta = 1; flops are 2mnk (Eq. 7) and algorithmic bytes read A and B once,
+    write C once and read C0 only when beta != 0."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    saved = sys.argv
+    try:
+        sys.argv = ["bench.py"]
+        pts = bench.workload_points(bench.parse())
+        sys.argv = ["bench.py", "--workload", "rankk"]
+        rk = bench.workload_points(bench.parse())
+    finally:
+        sys.argv = saved
+    assert len(pts) == 14 and bench.SWEEP_N == [1, 2, 4, 8, 16, 32, 64]
+    assert {(m, k) for (m, _, k, _) in pts} == {(32768, 32768)}
+    assert {b for (*_, b) in pts} == {0.0, 1.0}
+    assert [(m, n, k, b) for (m, n, k, b) in rk] == [(16384, 16384, k, 1.0) for k in (4, 8, 16, 32, 64, 128)]
+    assert bench.flops(3, 5, 7) == 210.0
+    assert bench.alg_bytes(10, 2, 3, 0.0, 4) == 4 * (30 + 6 + 20)
+    assert bench.alg_bytes(10, 2, 3, 0.5, 8) == 8 * (30 + 6 + 40)
+    # the derived FP32 peak: 152 SMs x 128 lanes x 2 flop x 2070 MHz
+    assert abs(bench.SMS * bench.FP32_LANES_PER_SM * 2 * bench.SM_MAX_MHZ * 1e6 / 1e12 - 80.55) < 0.01

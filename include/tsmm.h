@@ -310,10 +310,16 @@ TSMM_API int64_t tsmm_plan_cache_size(void);
  * items finish.
  * Each request's plan depends only on its shape, so its result is the same bit
  * for bit alone or in any mix.  The caller owns A, C and the packed B, and must
- * keep them alive until the request's completion has been polled.  The
- * server's streams are not ordered after the caller's: A, C0 and the packed B
- * must be in place on the device (the caller's streams synchronized) before
- * the request's arrival time.
+ * keep them alive until the request's completion has been polled.
+ *
+ * Ordering contract: the server's streams are not ordered after the caller's
+ * streams.  A, C0 (the prior content of C) and the packed B must be complete
+ * on the device -- the caller's streams that write them synchronized -- before
+ * the request's arrival time (before tsmm_server_submit for a request whose
+ * arrival time has already passed).  From submission until the request's
+ * completion has been polled the caller must not write A, C or the packed B
+ * and must not read C; after the completion is polled, C holds the result and
+ * no server work touches A, C or the packed B any more.
  */
 typedef struct tsmm_server_s *tsmm_server_t;
 
@@ -367,6 +373,19 @@ TSMM_API int64_t tsmm_server_poll(tsmm_server_t s, tsmm_completion *out, int64_t
 TSMM_API tsmm_status tsmm_server_destroy(tsmm_server_t s);
 /* The server's clock: steady, in seconds. */
 TSMM_API double tsmm_server_clock(void);
+
+/*
+ * tsmm_diag_server_inject_timeout -- diagnostics for the serving failure path
+ * (no counterpart in the paper).  The next `units` launch units the server
+ * starts finish as if a bounded wait in one of their kernels had run out:
+ * after the unit's kernels, on the unit's stream, its status word is set to the
+ * timeout record and the split-K arrival counters of its requests are left
+ * non-zero (what a block that gave up before taking its ticket leaves behind).
+ * The unit's requests then complete with TSMM_ERR_TIMEOUT, and the server
+ * must clear those counters before it hands them to later requests.  Nothing
+ * faults, traps or hangs.  Errors: INVALID_ARG for a NULL server or units < 0.
+ */
+TSMM_API tsmm_status tsmm_diag_server_inject_timeout(tsmm_server_t s, int units);
 
 /* Size of the library's built-in device scratch used by tsmm_execute_noalloc. */
 #define TSMM_NOALLOC_SCRATCH_BYTES (32u << 20)
@@ -426,6 +445,30 @@ TSMM_API tsmm_status tsmm_execute_noalloc(tsmm_dtype dtype, int64_t m, int64_t n
  * maximum SM clock.  Allocates and frees 16 bytes of device memory.
  */
 TSMM_API tsmm_status tsmm_diag_bounded_wait(uint32_t polls, uint64_t *cycles_out, double *seconds_out);
+
+/*
+ * tsmm_diag_fp_peak -- measures the throughput of one arithmetic pipe of the
+ * current GPU, for the roofline denominators of the compute-bound shapes
+ * (Eq. 7 rates are judged against it) and for the choice between the FP64
+ * FMA and FP64 MMA instructions (the GPU counterpart of the paper's
+ * install-time kernel selection, Section IV.B, decided by measurement).
+ *
+ * pipe: TSMM_DIAG_FFMA (FP32 fma), TSMM_DIAG_FFMA2 (packed FP32x2 fma, the
+ * instruction the FP32 kernels use), TSMM_DIAG_DFMA (FP64 fma),
+ * TSMM_DIAG_DMMA (FP64 mma.sync m8n8k4).  The kernel runs blocks_per_sm
+ * blocks of 256 threads on every SM; each thread runs independent chains of
+ * the instruction for `iters` loop trips.  One short untimed launch, then one
+ * timed launch between CUDA events on a private stream; synchronous.
+ * *flops_out: flops of the timed launch (2 per fma lane, 512 per DMMA warp
+ * instruction); *ms_out: its duration; *cycles_out: the longest block's SM
+ * clock cycles (cycles / ms gives the SM clock the launch ran at).  Output
+ * pointers may be NULL.  Errors: INVALID_ARG (pipe out of range, iters == 0,
+ * blocks_per_sm outside 1..8), CUDA.  Allocates and frees a few KB of device
+ * memory; changes no device setting.
+ */
+enum { TSMM_DIAG_FFMA = 0, TSMM_DIAG_FFMA2 = 1, TSMM_DIAG_DFMA = 2, TSMM_DIAG_DMMA = 3 };
+TSMM_API tsmm_status tsmm_diag_fp_peak(int pipe, uint32_t iters, int blocks_per_sm, double *flops_out,
+                                       double *ms_out, uint64_t *cycles_out);
 
 #ifdef __cplusplus
 }

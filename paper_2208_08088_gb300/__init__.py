@@ -32,15 +32,17 @@ __all__ = [
     "tsmm_plan_check", "tsmm_plan_launches_per_execute", "tsmm_autotune",
     "tsmm_plan_cache_load", "tsmm_plan_cache_save", "tsmm_plan_cache_clear", "tsmm_plan_cache_size",
     "tsmm_execute_noalloc", "tsmm_last_cuda_error", "tsmm_diag_bounded_wait", "diag_bounded_wait",
+    "tsmm_diag_fp_peak", "diag_fp_peak", "DIAG_FFMA", "DIAG_FFMA2", "DIAG_DFMA", "DIAG_DMMA",
     "autotune", "execute_grouped", "tsmm_execute_grouped", "GroupItem",
     "Server", "ServerConfig", "Request", "Completion", "tsmm_server_clock",
     "tsmm_server_create", "tsmm_server_submit", "tsmm_server_poll", "tsmm_server_drain",
-    "tsmm_server_destroy",
+    "tsmm_server_destroy", "tsmm_diag_server_inject_timeout",
     "PackedB", "Plan", "pack_b", "plan", "execute", "colmajor", "ld_of",
 ]
 
 F32, F64 = 0, 1
 PREC_NATIVE, PREC_BF16X3 = 0, 1
+DIAG_FFMA, DIAG_FFMA2, DIAG_DFMA, DIAG_DMMA = 0, 1, 2, 3
 STATUS = {
     0: "TSMM_OK", 1: "TSMM_ERR_INVALID_ARG", 2: "TSMM_ERR_UNSUPPORTED_SHAPE",
     3: "TSMM_ERR_MISMATCH", 4: "TSMM_ERR_MISALIGNED", 5: "TSMM_ERR_OUT_OF_MEMORY",
@@ -134,6 +136,8 @@ def _load():
     L.tsmm_server_poll.argtypes = [vp, ctypes.POINTER(Completion), i64]
     L.tsmm_server_destroy.restype = ci
     L.tsmm_server_destroy.argtypes = [vp]
+    L.tsmm_diag_server_inject_timeout.restype = ci
+    L.tsmm_diag_server_inject_timeout.argtypes = [vp, ci]
     L.tsmm_server_clock.restype = dbl
     L.tsmm_server_clock.argtypes = []
     L.tsmm_autotune.restype = ci
@@ -148,6 +152,9 @@ def _load():
     L.tsmm_diag_bounded_wait.restype = ci
     L.tsmm_diag_bounded_wait.argtypes = [ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint64),
                                          ctypes.POINTER(dbl)]
+    L.tsmm_diag_fp_peak.restype = ci
+    L.tsmm_diag_fp_peak.argtypes = [ci, ctypes.c_uint32, ci, ctypes.POINTER(dbl), ctypes.POINTER(dbl),
+                                    ctypes.POINTER(ctypes.c_uint64)]
     L.tsmm_execute_noalloc.restype = ci
     L.tsmm_execute_noalloc.argtypes = [ci, i64, i64, i64, dbl, vp, i64, vp, i64, dbl, vp, i64, vp]
     return L
@@ -437,6 +444,24 @@ def diag_bounded_wait(polls: int):
     return int(st), int(cyc.value), float(sec.value)
 
 
+def tsmm_diag_fp_peak(pipe: int, iters: int, blocks_per_sm: int = 4):
+    """Same-named form of diag_fp_peak: (flops, ms, cycles)."""
+    return diag_fp_peak(pipe, iters, blocks_per_sm)
+
+
+def diag_fp_peak(pipe: int, iters: int, blocks_per_sm: int = 4):
+    """Throughput of one arithmetic pipe (DIAG_FFMA, DIAG_FFMA2, DIAG_DFMA,
+    DIAG_DMMA) on the current GPU (tsmm_diag_fp_peak): returns (flops, ms,
+    cycles) of one timed launch; flops / ms is the rate, cycles / ms the SM
+    clock it ran at."""
+    fl = ctypes.c_double(0.0)
+    ms = ctypes.c_double(0.0)
+    cyc = ctypes.c_uint64(0)
+    _check(lib.tsmm_diag_fp_peak(int(pipe), int(iters), int(blocks_per_sm), ctypes.byref(fl),
+                                 ctypes.byref(ms), ctypes.byref(cyc)), "tsmm_diag_fp_peak")
+    return float(fl.value), float(ms.value), int(cyc.value)
+
+
 def autotune(A, pb: PackedB, C, reps: int = 5, stream=None) -> Plan:
     """Time candidate plans on these operands (C is overwritten), remember the
     winner in the plan cache and return a plan that uses it."""
@@ -488,6 +513,12 @@ def tsmm_server_destroy(server: int) -> None:
     _check(lib.tsmm_server_destroy(server), "tsmm_server_destroy")
 
 
+def tsmm_diag_server_inject_timeout(server: int, units: int) -> None:
+    """The next `units` launch units of the server finish as if a bounded wait
+    in their kernels had run out (diagnostics of the serving failure path)."""
+    _check(lib.tsmm_diag_server_inject_timeout(server, int(units)), "tsmm_diag_server_inject_timeout")
+
+
 class Server:
     """Owner of a tsmm_server_t: continuous batching of TSMM requests against
     device-resident packed B matrices (see include/tsmm.h)."""
@@ -525,6 +556,10 @@ class Server:
         n = int(lib.tsmm_server_poll(self.handle, buf, max_items))
         return [dict(id=c.id, arrival_s=c.arrival_s, admit_s=c.admit_s, launch_s=c.launch_s,
                      complete_s=c.complete_s, status=c.status) for c in buf[:n]]
+
+    def inject_timeout(self, units: int = 1) -> None:
+        """tsmm_diag_server_inject_timeout on this server."""
+        tsmm_diag_server_inject_timeout(self.handle, units)
 
     def close(self):
         if self.handle:

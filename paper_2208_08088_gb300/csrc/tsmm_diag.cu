@@ -55,3 +55,184 @@ extern "C" tsmm_status tsmm_diag_bounded_wait(uint32_t polls, uint64_t *cycles_o
     }
     return (host[0] & kDevErrTimeout) ? TSMM_ERR_TIMEOUT : TSMM_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Throughput of the arithmetic pipes the kernels are bound by, measured on
+// this GPU with the same harness for each: every thread runs CH independent
+// dependency chains of one instruction kind, and the grid fills every SM
+// with blocks_per_sm blocks of 256 threads, so issue and the pipe, not
+// latency, limit the rate.  The chains are x <- x*a + b with |a| < 1, so
+// values stay finite; the results are folded into a sink word that is
+// written only if the sum takes an impossible value, so nothing is
+// eliminated.  Thread 0 of each block records the block's SM cycles.
+namespace tsmm {
+namespace {
+
+constexpr int kPeakThreads = 256;
+
+__device__ __forceinline__ void peak_record(long long t0, unsigned long long *cycles) {
+    __syncthreads();
+    if (threadIdx.x == 0) cycles[blockIdx.x] = (unsigned long long)(clock64() - t0);
+}
+
+// FP32 scalar fma: 16 chains, 8 rounds per loop trip (128 FFMA per 3 loop instructions).
+__global__ void __launch_bounds__(kPeakThreads) peak_ffma_kernel(uint32_t iters, float a, float b, float *sink,
+                                                                  unsigned long long *cycles) {
+    const long long t0 = clock64();
+    float x[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) x[i] = b * (float)(threadIdx.x + i);
+    for (uint32_t it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+#pragma unroll
+            for (int i = 0; i < 16; ++i) x[i] = fmaf(x[i], a, b);
+    }
+    float s = 0.f;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) s += x[i];
+    if (s == -1.2345e30f) sink[0] = s;
+    peak_record(t0, cycles);
+}
+
+// FP32 packed pair fma (fma.rn.f32x2): 16 chains of float2, 8 rounds per trip.
+__global__ void __launch_bounds__(kPeakThreads) peak_ffma2_kernel(uint32_t iters, float a, float b, float *sink,
+                                                                   unsigned long long *cycles) {
+    const long long t0 = clock64();
+    const float2 a2 = make_float2(a, a);
+    const float2 b2 = make_float2(b, b);
+    float2 x[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) x[i] = make_float2(b * (float)(threadIdx.x + i), b * (float)i);
+    for (uint32_t it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+#pragma unroll
+            for (int i = 0; i < 16; ++i) x[i] = __ffma2_rn(x[i], a2, b2);
+    }
+    float s = 0.f;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) s += x[i].x + x[i].y;
+    if (s == -1.2345e30f) sink[0] = s;
+    peak_record(t0, cycles);
+}
+
+// FP64 fma: 8 chains, 4 rounds per trip.
+__global__ void __launch_bounds__(kPeakThreads) peak_dfma_kernel(uint32_t iters, double a, double b, float *sink,
+                                                                  unsigned long long *cycles) {
+    const long long t0 = clock64();
+    double x[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) x[i] = b * (double)(threadIdx.x + i);
+    for (uint32_t it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int i = 0; i < 8; ++i) x[i] = fma(x[i], a, b);
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) s += x[i];
+    if (s == -1.2345e300) sink[0] = (float)s;
+    peak_record(t0, cycles);
+}
+
+// FP64 tensor-core MMA (mma.sync m8n8k4, 512 flop per warp instruction):
+// 8 independent accumulator fragments per warp, 4 rounds per trip.  The A and
+// B fragments are constant, so D <- A*B + D grows by the same small product
+// each step.
+__global__ void __launch_bounds__(kPeakThreads) peak_dmma_kernel(uint32_t iters, double a, double b, float *sink,
+                                                                  unsigned long long *cycles) {
+    const long long t0 = clock64();
+    double d[8][2];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        d[i][0] = b * (double)(threadIdx.x + i);
+        d[i][1] = b * (double)i;
+    }
+    const double fa = a * 1e-3, fb = b * 1e-3;
+    for (uint32_t it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+                asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0, %1}, {%2}, {%3}, {%0, %1};"
+                             : "+d"(d[i][0]), "+d"(d[i][1])
+                             : "d"(fa), "d"(fb));
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) s += d[i][0] + d[i][1];
+    if (s == -1.2345e300) sink[0] = (float)s;
+    peak_record(t0, cycles);
+}
+
+// flops one launch of `pipe` executes per thread per loop trip
+double peak_flops_per_thread_trip(int pipe) {
+    switch (pipe) {
+        case TSMM_DIAG_FFMA: return 8.0 * 16 * 2;
+        case TSMM_DIAG_FFMA2: return 8.0 * 16 * 4;
+        case TSMM_DIAG_DFMA: return 4.0 * 8 * 2;
+        default: return 4.0 * 8 * 512 / 32;  // DMMA: 512 flop per warp instruction
+    }
+}
+
+cudaError_t peak_launch(int pipe, unsigned grid, uint32_t iters, float *sink, unsigned long long *cycles,
+                        cudaStream_t s) {
+    switch (pipe) {
+        case TSMM_DIAG_FFMA: peak_ffma_kernel<<<grid, kPeakThreads, 0, s>>>(iters, 0.999f, 1e-3f, sink, cycles); break;
+        case TSMM_DIAG_FFMA2: peak_ffma2_kernel<<<grid, kPeakThreads, 0, s>>>(iters, 0.999f, 1e-3f, sink, cycles); break;
+        case TSMM_DIAG_DFMA: peak_dfma_kernel<<<grid, kPeakThreads, 0, s>>>(iters, 0.999, 1e-3, sink, cycles); break;
+        default: peak_dmma_kernel<<<grid, kPeakThreads, 0, s>>>(iters, 0.999, 1e-3, sink, cycles); break;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace
+}  // namespace tsmm
+
+extern "C" tsmm_status tsmm_diag_fp_peak(int pipe, uint32_t iters, int blocks_per_sm, double *flops_out,
+                                         double *ms_out, uint64_t *cycles_out) {
+    if (pipe < TSMM_DIAG_FFMA || pipe > TSMM_DIAG_DMMA || iters == 0 || blocks_per_sm < 1 || blocks_per_sm > 8)
+        return TSMM_ERR_INVALID_ARG;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
+        return TSMM_ERR_CUDA;
+    const unsigned grid = (unsigned)(sms * blocks_per_sm);
+    void *buf = nullptr;
+    const size_t bytes = 256 + (size_t)grid * sizeof(unsigned long long);
+    if (cudaMalloc(&buf, bytes) != cudaSuccess) return TSMM_ERR_CUDA;
+    float *sink = static_cast<float *>(buf);
+    unsigned long long *cycles = reinterpret_cast<unsigned long long *>(static_cast<char *>(buf) + 256);
+    cudaStream_t s = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    tsmm_status st = TSMM_OK;
+    float ms = 0.f;
+    unsigned long long *host = new unsigned long long[grid];
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+        cudaEventCreate(&e1) != cudaSuccess) {
+        st = TSMM_ERR_CUDA;
+    } else {
+        // one short untimed launch (module load, clocks up), then the timed one
+        const uint32_t warm = iters / 8 > 0 ? iters / 8 : 1;
+        if (peak_launch(pipe, grid, warm, sink, cycles, s) != cudaSuccess || cudaEventRecord(e0, s) != cudaSuccess ||
+            peak_launch(pipe, grid, iters, sink, cycles, s) != cudaSuccess || cudaEventRecord(e1, s) != cudaSuccess ||
+            cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess ||
+            cudaMemcpy(host, cycles, grid * sizeof(unsigned long long), cudaMemcpyDeviceToHost) != cudaSuccess)
+            st = TSMM_ERR_CUDA;
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (s) cudaStreamDestroy(s);
+    cudaFree(buf);
+    if (st == TSMM_OK) {
+        unsigned long long mx = 0;
+        for (unsigned i = 0; i < grid; ++i) mx = host[i] > mx ? host[i] : mx;
+        if (flops_out) *flops_out = peak_flops_per_thread_trip(pipe) * (double)iters * kPeakThreads * grid;
+        if (ms_out) *ms_out = (double)ms;
+        if (cycles_out) *cycles_out = mx;
+    }
+    delete[] host;
+    return st;
+}

@@ -21,7 +21,12 @@
 //     launched small work as items finish instead of after a whole persistent
 //     launch;
 //   * detects sub-batch completion with CUDA events, records completion times
-//     and returns the sub-batch's memory to the budget and the arena.
+//     and returns the sub-batch's memory to the budget and the arena.  Each
+//     launch unit has its own device status word, so a bounded wait that gave
+//     up is charged to the unit whose kernel gave up.  A unit that failed may
+//     have left split-K arrival counters part-way (a block that gave up never
+//     takes its ticket): its counter slices are cleared on its own stream, and
+//     only returned to the arena once that clear has completed.
 // Results are deterministic: each request's plan depends only on its shape,
 // never on what else is in flight.
 #include <algorithm>
@@ -100,8 +105,21 @@ struct Req {
 struct Batch {
     std::vector<Req *> reqs;
     cudaEvent_t ev = nullptr;
+    cudaStream_t st = nullptr;  // the stream its kernels (and a clean-up) run on
     int lane = -1;
+    int slot = -1;              // its status word
+    int fail = TSMM_OK;         // status decided before the event completes
+    bool cleaning = false;      // the event now marks the end of the counter clean-up
 };
+
+// Status words (mapped, pinned host memory; one per launch unit in flight).
+// A launch has at most one unit per kernel class plus kMaxSubBatches - 1, on
+// at most 16 lanes: far below this.
+constexpr int kStatusSlots = 1024;
+
+// Diagnostics: the effect a kernel that gave up on a bounded wait leaves
+// behind -- its status word set -- written by a kernel of its own.
+__global__ void diag_flag_timeout_kernel(unsigned *status) { atomicOr(status, kDevErrTimeout); }
 
 // Sub-batches per launch (requests in ascending order of bytes, A + C +
 // workspace): a new sub-batch starts at a request that alone holds at least as
@@ -125,9 +143,11 @@ struct tsmm_server_s {
     std::vector<cudaEvent_t> free_events;  // not recorded by an in-flight unit
     void *ws_base = nullptr;
     void *tk_base = nullptr;
-    unsigned *status_host = nullptr;  // mapped, pinned
-    unsigned *status_dev = nullptr;   // its device address
+    unsigned *status_host = nullptr;  // kStatusSlots words, mapped, pinned
+    unsigned *status_dev = nullptr;   // their device address
+    std::vector<int> free_slots;
     Arena ws_arena, tk_arena;
+    std::atomic<int> inject_units{0};  // tsmm_diag_server_inject_timeout
 
     std::mutex mu;
     std::condition_variable cv_done;
@@ -149,6 +169,7 @@ struct tsmm_server_s {
     void launch(double t);
     bool poll_batches();
     void finish(Batch &b, int status, double t);
+    bool start_cleanup(Batch &b, int status);
 };
 
 bool tsmm_server_s::try_admit(Req *q, double t) {
@@ -162,7 +183,7 @@ bool tsmm_server_s::try_admit(Req *q, double t) {
     q->plan.tickets = q->ticket_bytes
                           ? reinterpret_cast<unsigned *>(static_cast<char *>(tk_base) + q->tk_off)
                           : nullptr;
-    q->plan.status = status_dev;
+    q->plan.status = nullptr;  // the launch unit's own word, set in launch()
     q->admit_s = t;
     inflight_bytes += q->bytes;
     return true;
@@ -215,13 +236,8 @@ void tsmm_server_s::launch(double t) {
     for (Unit &u : units) {
         Batch b;
         b.reqs = std::move(u.reqs);
+        b.st = u.st;
         if (st == TSMM_OK) {
-            std::vector<tsmm_group_item> items(b.reqs.size());
-            for (size_t i = 0; i < b.reqs.size(); ++i) {
-                const tsmm_request &r = b.reqs[i]->r;
-                items[i] = tsmm_group_item{&b.reqs[i]->plan, r.alpha, r.A_dev, r.lda, r.pb, r.beta, r.C_dev,
-                                           r.ldc};
-            }
             if (free_events.empty()) {
                 cudaEvent_t ev;
                 if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess) {
@@ -229,27 +245,85 @@ void tsmm_server_s::launch(double t) {
                     free_events.push_back(ev);
                 }
             }
-            if (free_events.empty()) {
-                st = TSMM_ERR_CUDA;
+            if (free_events.empty() || free_slots.empty()) {
+                st = TSMM_ERR_CUDA;  // nothing of this unit was enqueued
             } else {
                 b.ev = free_events.back();
                 free_events.pop_back();
+                b.slot = free_slots.back();
+                free_slots.pop_back();
+                status_host[b.slot] = 0u;
+                std::vector<tsmm_group_item> items(b.reqs.size());
+                for (size_t i = 0; i < b.reqs.size(); ++i) {
+                    Req *q = b.reqs[i];
+                    q->plan.status = status_dev + b.slot;
+                    const tsmm_request &r = q->r;
+                    items[i] = tsmm_group_item{&q->plan, r.alpha, r.A_dev, r.lda, r.pb, r.beta, r.C_dev, r.ldc};
+                }
                 st = execute_grouped(items.data(), (int)items.size(), u.st, u.persistent);
-                if (st == TSMM_OK && cudaEventRecord(b.ev, u.st) != cudaSuccess) st = TSMM_ERR_CUDA;
+                if (st == TSMM_OK && inject_units.load() > 0) {
+                    // diagnostics: leave what a block that gave up leaves -- the unit's
+                    // status word set and its arrival counters part-way
+                    --inject_units;
+                    diag_flag_timeout_kernel<<<1, 1, 0, u.st>>>(status_dev + b.slot);
+                    for (Req *q : b.reqs)
+                        if (q->ticket_bytes) cudaMemsetAsync(q->plan.tickets, 0x01, q->ticket_bytes, u.st);
+                    if (cudaGetLastError() != cudaSuccess) st = TSMM_ERR_CUDA;
+                }
+                // Recorded even when the launch failed: kernels enqueued before the
+                // failure may still be running, and the unit's memory stays in use
+                // until they are done.
+                if (cudaEventRecord(b.ev, u.st) != cudaSuccess) {
+                    cudaStreamSynchronize(u.st);
+                    cudaGetLastError();
+                    if (st == TSMM_OK) st = TSMM_ERR_CUDA;
+                    finish(b, st, now_s());
+                    continue;
+                }
             }
-            if (st == TSMM_OK) {
+            if (b.ev) {
                 b.lane = s;
+                b.fail = st;
                 ++lane_pending[s];
                 inflight.push_back(std::move(b));
                 continue;
             }
         }
-        finish(b, st, now_s());  // this unit and the ones after it fail
+        finish(b, st, now_s());  // a unit after a failed one: nothing of it was enqueued
     }
+}
+
+// A unit finished with an error: its split-K arrival counters may be left
+// part-way, which would make the next request given the same slices pick the
+// wrong last-arriving block.  Clear them on the unit's stream and keep the
+// unit in flight until the clear is done.  Returns false (and waits for the
+// stream) if the clear could not be enqueued.
+bool tsmm_server_s::start_cleanup(Batch &b, int status) {
+    bool any = false;
+    cudaError_t e = cudaSuccess;
+    for (Req *q : b.reqs)
+        if (q->ticket_bytes && e == cudaSuccess) {
+            e = cudaMemsetAsync(q->plan.tickets, 0, q->ticket_bytes, b.st);
+            any = true;
+        }
+    if (!any) return false;
+    if (e == cudaSuccess) e = cudaEventRecord(b.ev, b.st);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        for (Req *q : b.reqs)
+            if (q->ticket_bytes) cudaMemset(q->plan.tickets, 0, q->ticket_bytes);
+        cudaDeviceSynchronize();
+        cudaGetLastError();
+        return false;
+    }
+    b.cleaning = true;
+    b.fail = status;
+    return true;
 }
 
 void tsmm_server_s::finish(Batch &b, int status, double t) {
     if (b.ev) free_events.push_back(b.ev);
+    if (b.slot >= 0) free_slots.push_back(b.slot);
     std::lock_guard<std::mutex> lock(mu);
     for (Req *q : b.reqs) {
         inflight_bytes -= q->bytes;
@@ -267,21 +341,30 @@ void tsmm_server_s::finish(Batch &b, int status, double t) {
 bool tsmm_server_s::poll_batches() {
     bool progress = false;
     for (size_t i = 0; i < inflight.size();) {
-        cudaError_t e = cudaEventQuery(inflight[i].ev);
+        Batch &ib = inflight[i];
+        cudaError_t e = cudaEventQuery(ib.ev);
         if (e == cudaErrorNotReady) {
             ++i;
             continue;
         }
-        int status = e == cudaSuccess ? TSMM_OK : TSMM_ERR_CUDA;
-        // the kernels' give-up record lives in mapped host memory: read it directly
-        if (e == cudaSuccess && *reinterpret_cast<volatile unsigned *>(status_host) != 0u) {
-            status = TSMM_ERR_TIMEOUT;
-            *reinterpret_cast<volatile unsigned *>(status_host) = 0u;
+        progress = true;
+        int status = ib.fail;
+        if (!ib.cleaning) {
+            if (e != cudaSuccess) status = TSMM_ERR_CUDA;
+            // this unit's give-up record lives in mapped host memory: read it directly
+            volatile unsigned *word = status_host + ib.slot;
+            if (e == cudaSuccess && *word != 0u) {
+                if (status == TSMM_OK) status = TSMM_ERR_TIMEOUT;
+                *word = 0u;
+            }
+            if (status != TSMM_OK && start_cleanup(ib, status)) {
+                ++i;  // finished once the clear has completed
+                continue;
+            }
         }
-        Batch b = std::move(inflight[i]);
+        Batch b = std::move(ib);
         inflight.erase(inflight.begin() + i);
         finish(b, status, now_s());
-        progress = true;
     }
     return progress;
 }
@@ -338,9 +421,10 @@ tsmm_status tsmm_server_create(const tsmm_server_config *cfg, tsmm_server_t *out
     if (e == cudaSuccess) e = cudaMalloc(&s->tk_base, tk_bytes);
     if (e == cudaSuccess) e = cudaMemset(s->tk_base, 0, tk_bytes);  // arrival counters start at 0
     if (e == cudaSuccess)
-        e = cudaHostAlloc(reinterpret_cast<void **>(&s->status_host), sizeof(unsigned), cudaHostAllocMapped);
+        e = cudaHostAlloc(reinterpret_cast<void **>(&s->status_host), kStatusSlots * sizeof(unsigned),
+                          cudaHostAllocMapped);
     if (e == cudaSuccess) {
-        *s->status_host = 0u;
+        for (int i = 0; i < kStatusSlots; ++i) s->status_host[i] = 0u;
         e = cudaHostGetDevicePointer(reinterpret_cast<void **>(&s->status_dev), s->status_host, 0);
     }
     int prio_low = 0, prio_high = 0;
@@ -369,6 +453,7 @@ tsmm_status tsmm_server_create(const tsmm_server_config *cfg, tsmm_server_t *out
     }
     s->lane_pending.assign(cfg->num_streams, 0);
     s->free_events = s->events;
+    for (int i = kStatusSlots - 1; i >= 0; --i) s->free_slots.push_back(i);
     s->ws_arena.init(s->cfg.arena_bytes);
     s->tk_arena.init(tk_bytes);
     s->th = std::thread([s] { s->run(); });
@@ -440,6 +525,12 @@ tsmm_status tsmm_server_drain(tsmm_server_t s, double timeout_s) {
     const bool ok = s->cv_done.wait_for(lock, std::chrono::duration<double>(timeout_s),
                                         [s] { return s->completed >= s->submitted; });
     return ok ? TSMM_OK : TSMM_ERR_TIMEOUT;
+}
+
+tsmm_status tsmm_diag_server_inject_timeout(tsmm_server_t s, int units) {
+    if (!s || units < 0) return TSMM_ERR_INVALID_ARG;
+    s->inject_units.store(units);
+    return TSMM_OK;
 }
 
 tsmm_status tsmm_server_destroy(tsmm_server_t s) {

@@ -124,3 +124,15 @@ def test_noalloc_argument_errors_before_device_work():
     assert e.value.status == 1
     # m = 0 or n = 0: nothing to do, no device touched
     tsmm.tsmm_execute_noalloc(tsmm.F32, 0, 8, 8, 1.0, 0, 1, 0, 8, 0.0, 0, 1)
+
+
+def test_fp_peak_argument_errors_before_device_work():
+    L = tsmm.lib
+    assert L.tsmm_diag_fp_peak(4, 10, 4, None, None, None) == 1   # no such pipe
+    assert L.tsmm_diag_fp_peak(-1, 10, 4, None, None, None) == 1
+    assert L.tsmm_diag_fp_peak(0, 0, 4, None, None, None) == 1    # iters == 0
+    assert L.tsmm_diag_fp_peak(0, 10, 0, None, None, None) == 1   # blocks per SM outside 1..8
+    assert L.tsmm_diag_fp_peak(0, 10, 9, None, None, None) == 1
+    with pytest.raises(tsmm.TsmmError) as e:
+        tsmm.diag_fp_peak(tsmm.DIAG_DMMA, 0)
+    assert e.value.status == 1

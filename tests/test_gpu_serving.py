@@ -154,3 +154,62 @@ def test_serving_small_requests_finish_before_a_large_one_of_their_batch():
         Cref, E = oracle.tsmm(1.0, A, B_s, 0.0, None)
         ok, ratio, nbad = oracle.check(dC.cpu().numpy(), Cref, E, np.float32)
         assert ok, f"request {rid}: {nbad} entries outside the bound"
+
+
+def _split_k_request(rid, m, n, k, seed):
+    A = ti.matrix_np(m, k, seed, "uniform", np.float32)
+    B = ti.matrix_np(k, n, seed + 1, "uniform", np.float32)
+    C0 = ti.matrix_np(m, n, seed + 2, "uniform", np.float32)
+    pb = tsmm.pack_b(to_device(B))
+    return dict(id=rid, A=A, B=B, C0=C0, pb=pb, dA=to_device(A), dC=to_device(C0))
+
+
+def _submit(server, reqs, alpha=1.5, beta=0.5):
+    torch.cuda.synchronize()  # inputs in place before submission (the server's ordering contract)
+    t0 = tsmm.tsmm_server_clock()
+    server.submit([(q["id"], q["pb"], q["A"].shape[0], alpha, q["dA"], beta, q["dC"], t0) for q in reqs])
+    server.drain(60.0)
+    return {c["id"]: c for c in server.poll()}
+
+
+def test_serving_timeout_clears_split_k_counters():
+    """A launch unit whose kernels gave up (injected on the host: status word set,
+    arrival counters left part-way, as a block that gave up before its ticket
+    leaves them) completes with TSMM_ERR_TIMEOUT, and the next split-K request,
+    which the arena hands the same counter slice, is still exact: the server
+    cleared the counters before releasing them."""
+    m, n, k = 300, 16, 20000
+    assert tsmm.plan(m, n, k, torch.float32).info()["splits"] > 1  # split-K: counters in use
+    srv = tsmm.Server(budget_bytes=1 << 30, num_streams=1, max_batch=1)
+    try:
+        first = _split_k_request(0, m, n, k, 700)
+        srv.inject_timeout(1)
+        comps = _submit(srv, [first])
+        assert comps[0]["status"] == 7  # TSMM_ERR_TIMEOUT
+        for rid in (1, 2):  # follow-ups reuse the cleared slice
+            q = _split_k_request(rid, m, n, k, 700 + 10 * rid)
+            comps = _submit(srv, [q])
+            assert comps[rid]["status"] == 0
+            Cref, E = oracle.tsmm(1.5, q["A"], q["B"], 0.5, q["C0"])
+            ok, ratio, nbad = oracle.check(q["dC"].cpu().numpy(), Cref, E, np.float32)
+            assert ok, f"follow-up {rid}: {nbad} entries outside the bound (max ratio {ratio:.3g})"
+    finally:
+        srv.close()
+
+
+def test_serving_timeout_charged_to_its_own_unit():
+    """Two requests launched as separate units on two lanes, the first with an
+    injected timeout: only that one reports TSMM_ERR_TIMEOUT; the other completes
+    OK and matches the oracle (each launch unit has its own status word)."""
+    m, n, k = 300, 16, 20000
+    srv = tsmm.Server(budget_bytes=1 << 30, num_streams=2, max_batch=1)
+    try:
+        qs = [_split_k_request(rid, m, n, k, 800 + 10 * rid) for rid in range(2)]
+        srv.inject_timeout(1)
+        comps = _submit(srv, qs)
+        assert comps[0]["status"] == 7 and comps[1]["status"] == 0
+        Cref, E = oracle.tsmm(1.5, qs[1]["A"], qs[1]["B"], 0.5, qs[1]["C0"])
+        ok, ratio, nbad = oracle.check(qs[1]["dC"].cpu().numpy(), Cref, E, np.float32)
+        assert ok, f"{nbad} entries outside the bound (max ratio {ratio:.3g})"
+    finally:
+        srv.close()

@@ -117,52 +117,81 @@ __global__ void __launch_bounds__(kPeakThreads) peak_ffma2_kernel(uint32_t iters
     peak_record(t0, cycles);
 }
 
-// FP64 fma: 8 chains, 4 rounds per trip.
+// Operands of the FP64 probes live in shared memory and are read afresh every
+// step, as the TSMM kernels read theirs.  (FP64
+// fmas whose operands all stay in registers run at about 0.84 of the pipe's
+// rate on GB300; with operands from shared memory the pipe saturates, as it
+// does in the FP64 TSMM kernels.)
+__device__ __forceinline__ void peak_fill_f64(double *s, int n) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s[i] = 0.5 + 1e-3 * (double)(i % 61);
+    __syncthreads();
+}
+
+// FP64 fma: a 4 x 4 accumulator tile per thread, 4 + 4 operands from shared
+// memory per step (row p = trip mod 64), 16 fmas.
 __global__ void __launch_bounds__(kPeakThreads) peak_dfma_kernel(uint32_t iters, double a, double b, float *sink,
                                                                   unsigned long long *cycles) {
     const long long t0 = clock64();
-    double x[8];
+    __shared__ double sa[64 * 4], sb[64 * 4];
+    peak_fill_f64(sa, 64 * 4);
+    peak_fill_f64(sb, 64 * 4);
+    double acc[4][4];
 #pragma unroll
-    for (int i = 0; i < 8; ++i) x[i] = b * (double)(threadIdx.x + i);
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[r][c] = a * b;
     for (uint32_t it = 0; it < iters; ++it) {
+        const int p = (int)(it & 63);
+        double av[4], bv[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
+        for (int r = 0; r < 4; ++r) av[r] = sa[p * 4 + r];
 #pragma unroll
-            for (int i = 0; i < 8; ++i) x[i] = fma(x[i], a, b);
+        for (int c = 0; c < 4; ++c) bv[c] = sb[p * 4 + c];
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[r][c] = fma(av[r], bv[c], acc[r][c]);
     }
     double s = 0.0;
 #pragma unroll
-    for (int i = 0; i < 8; ++i) s += x[i];
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) s += acc[r][c];
     if (s == -1.2345e300) sink[0] = (float)s;
     peak_record(t0, cycles);
 }
 
-// FP64 tensor-core MMA (mma.sync m8n8k4, 512 flop per warp instruction):
-// 8 independent accumulator fragments per warp, 4 rounds per trip.  The A and
-// B fragments are constant, so D <- A*B + D grows by the same small product
-// each step.
+// FP64 tensor-core MMA (mma.sync m8n8k4, 512 flop per warp instruction): per
+// step 2 A and 4 B fragments from shared memory (16 rows of 6 fragments, row
+// p = trip mod 16) and 8 independent accumulator fragments, D[x][y] += A_x * B_y.
 __global__ void __launch_bounds__(kPeakThreads) peak_dmma_kernel(uint32_t iters, double a, double b, float *sink,
                                                                   unsigned long long *cycles) {
     const long long t0 = clock64();
-    double d[8][2];
+    __shared__ double sf[16 * 6 * 32];
+    peak_fill_f64(sf, 16 * 6 * 32);
+    const int lane = threadIdx.x % 32;
+    double d[2][4][2];
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        d[i][0] = b * (double)(threadIdx.x + i);
-        d[i][1] = b * (double)i;
-    }
-    const double fa = a * 1e-3, fb = b * 1e-3;
+    for (int x = 0; x < 2; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) d[x][y][0] = d[x][y][1] = a * b;
     for (uint32_t it = 0; it < iters; ++it) {
+        const double *f = sf + (int)(it & 15) * 6 * 32 + lane;
+        const double fa[2] = {f[0], f[32]};
+        const double fb[4] = {f[64], f[96], f[128], f[160]};
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
+        for (int x = 0; x < 2; ++x)
 #pragma unroll
-            for (int i = 0; i < 8; ++i)
+            for (int y = 0; y < 4; ++y)
                 asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0, %1}, {%2}, {%3}, {%0, %1};"
-                             : "+d"(d[i][0]), "+d"(d[i][1])
-                             : "d"(fa), "d"(fb));
+                             : "+d"(d[x][y][0]), "+d"(d[x][y][1])
+                             : "d"(fa[x]), "d"(fb[y]));
     }
     double s = 0.0;
 #pragma unroll
-    for (int i = 0; i < 8; ++i) s += d[i][0] + d[i][1];
+    for (int x = 0; x < 2; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) s += d[x][y][0] + d[x][y][1];
     if (s == -1.2345e300) sink[0] = (float)s;
     peak_record(t0, cycles);
 }
@@ -172,8 +201,8 @@ double peak_flops_per_thread_trip(int pipe) {
     switch (pipe) {
         case TSMM_DIAG_FFMA: return 8.0 * 16 * 2;
         case TSMM_DIAG_FFMA2: return 8.0 * 16 * 4;
-        case TSMM_DIAG_DFMA: return 4.0 * 8 * 2;
-        default: return 4.0 * 8 * 512 / 32;  // DMMA: 512 flop per warp instruction
+        case TSMM_DIAG_DFMA: return 16.0 * 2;
+        default: return 8.0 * 512 / 32;  // DMMA: 512 flop per warp instruction
     }
 }
 

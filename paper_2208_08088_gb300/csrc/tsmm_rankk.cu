@@ -479,29 +479,32 @@ struct WideCfg {
 };
 
 struct WideAcc {
-    float2 v[4][8];  // [row pair][column]
+    // [row][column pair]: rows r0..r0+3 (0..3) and r0+32..r0+35 (4..7); column
+    // pairs (c0, c0+1), (c0+2, c0+3), (c0+16, c0+17), (c0+18, c0+19).  Each A
+    // value is duplicated into both halves of a packed operand and B supplies
+    // adjacent column pairs as they lie in shared memory.
+    float2 v[8][4];
     __device__ __forceinline__ void zero() {
 #pragma unroll
-        for (int rp = 0; rp < 4; ++rp)
+        for (int r = 0; r < 8; ++r)
 #pragma unroll
-            for (int c = 0; c < 8; ++c) v[rp][c] = make_float2(0.f, 0.f);
+            for (int q = 0; q < 4; ++q) v[r][q] = make_float2(0.f, 0.f);
     }
-    // row pairs rp: {r0 + 2rp, +1} for rp < 2, {r0 + 32 + 2(rp - 2), +1} after;
-    // columns c: c0 + c for c < 4, c0 + 16 + (c - 4) after
     __device__ __forceinline__ void step(const float *As, const float *Bs, int pc, int r0, int c0) {
         const float4 a0 = *reinterpret_cast<const float4 *>(As + pc * 128 + r0);
         const float4 a1 = *reinterpret_cast<const float4 *>(As + pc * 128 + r0 + 32);
         const float4 b0 = *reinterpret_cast<const float4 *>(Bs + pc * kRankNT + c0);
         const float4 b1 = *reinterpret_cast<const float4 *>(Bs + pc * kRankNT + c0 + 16);
-        const float2 ap[4] = {make_float2(a0.x, a0.y), make_float2(a0.z, a0.w), make_float2(a1.x, a1.y),
-                              make_float2(a1.z, a1.w)};
-        const float bs[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+        const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+        const float2 bp[4] = {make_float2(b0.x, b0.y), make_float2(b0.z, b0.w), make_float2(b1.x, b1.y),
+                              make_float2(b1.z, b1.w)};
+        float2 ad[8];
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
-            const float2 bd = make_float2(bs[c], bs[c]);
+        for (int r = 0; r < 8; ++r) ad[r] = make_float2(av[r], av[r]);
 #pragma unroll
-            for (int rp = 0; rp < 4; ++rp) v[rp][c] = __ffma2_rn(ap[rp], bd, v[rp][c]);
-        }
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int r = 0; r < 8; ++r) v[r][q] = __ffma2_rn(ad[r], bp[q], v[r][q]);
     }
     // a full chunk is unrolled whole, so its loads can be scheduled early
     template <int KC>
@@ -516,9 +519,9 @@ struct WideAcc {
     }
     // the 4 rows of row group rg (0: r0.., 1: r0+32..) in column c (0..7)
     __device__ __forceinline__ float4 rows(int rg, int c) const {
-        const float2 lo = v[rg * 2][c];
-        const float2 hi = v[rg * 2 + 1][c];
-        return make_float4(lo.x, lo.y, hi.x, hi.y);
+        const int q = c / 2;
+        if (c & 1) return make_float4(v[rg * 4][q].y, v[rg * 4 + 1][q].y, v[rg * 4 + 2][q].y, v[rg * 4 + 3][q].y);
+        return make_float4(v[rg * 4][q].x, v[rg * 4 + 1][q].x, v[rg * 4 + 2][q].x, v[rg * 4 + 3][q].x);
     }
 };
 

@@ -269,6 +269,20 @@ def test_rankk_persistent_many_tiles(dtype, k, beta, m):
     assert_parity(C, A, B, C0 if beta != 0 else None, 1.0 if k != 33 else 0.75, beta)
 
 
+@pytest.mark.parametrize("beta", [0.0, 1.0])
+@pytest.mark.parametrize("k", [33, 64, 128])
+@pytest.mark.parametrize("m,n", [(129, 65), (1000, 80), (1000, 96), (384, 97), (1000, 130), (2048, 1000)])
+def test_rankk_tma_epilogue_edges_integer_exact(m, n, k, beta):
+    """FP32 with k > 32 and C meeting the TMA rules (m = 129 does not: the plain
+    epilogue) moves C0 and C as 128 x 64 tiles by tensor copies: ragged m and n
+    whose last tile is a quarter to seven eighths beyond n, beta = 0 over a
+    NaN-filled C, integer inputs (exact)."""
+    A, B, C0 = gen(m, n, k, np.float32, "integer")
+    C, pl, _ = run(A, B, C0 if beta != 0 else None, 1.5, beta)
+    assert pl.info()["regime"] == 2
+    assert_parity(C, A, B, C0 if beta != 0 else None, 1.5, beta, exact=True)
+
+
 @pytest.mark.parametrize("k", [1, 8, 32])
 def test_rankk_f64_alpha_beta_one_integer_exact(k):
     """FP64 with alpha = beta = 1 and k within one chunk starts its

@@ -679,7 +679,7 @@ __global__ void __launch_bounds__(WideCfg<TMA_EPI, KC>::THREADS, WideCfg<TMA_EPI
             if (lane == 0) mbar_arrive(&empty[st]);
         }
         if (!ok) break;
-        if (TMA_EPI) {
+        if constexpr (TMA_EPI) {
             if (!__all_sync(0xffffffffu, mbar_wait_bounded(cfull, (uint32_t)(j & 1)))) {
                 ok = false;
                 break;
@@ -698,48 +698,48 @@ __global__ void __launch_bounds__(WideCfg<TMA_EPI, KC>::THREADS, WideCfg<TMA_EPI
             fence_proxy_async_smem();
             __syncwarp();
             if (lane == 0) mbar_arrive(cstore);
-            continue;
-        }
-        // plain epilogue in two halves of 4 columns: all C0 loads of a half before its stores
+        } else {
+            // plain epilogue in two halves of 4 columns: all C0 loads of a half before its stores
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            float4 c0v[4][2];
+            for (int h = 0; h < 2; ++h) {
+                float4 c0v[4][2];
 #pragma unroll
-            for (int cc = 0; cc < 4; ++cc) {
-                const int64_t jg = tile * W::BNT + c0 + h * 16 + cc;
+                for (int cc = 0; cc < 4; ++cc) {
+                    const int64_t jg = tile * W::BNT + c0 + h * 16 + cc;
 #pragma unroll
-                for (int rg = 0; rg < 2; ++rg) {
-                    const int64_t i = i0 + r0 + rg * 32;
-                    c0v[cc][rg] = make_float4(0.f, 0.f, 0.f, 0.f);
-                    if (!use_c0 || jg >= a.n) continue;
-                    const float *src = C + i + jg * a.ldc;
-                    if (vec_c && i + 4 <= a.m) {
-                        c0v[cc][rg] = *reinterpret_cast<const float4 *>(src);
-                    } else {
-                        if (i < a.m) c0v[cc][rg].x = src[0];
-                        if (i + 1 < a.m) c0v[cc][rg].y = src[1];
-                        if (i + 2 < a.m) c0v[cc][rg].z = src[2];
-                        if (i + 3 < a.m) c0v[cc][rg].w = src[3];
+                    for (int rg = 0; rg < 2; ++rg) {
+                        const int64_t i = i0 + r0 + rg * 32;
+                        c0v[cc][rg] = make_float4(0.f, 0.f, 0.f, 0.f);
+                        if (!use_c0 || jg >= a.n) continue;
+                        const float *src = C + i + jg * a.ldc;
+                        if (vec_c && i + 4 <= a.m) {
+                            c0v[cc][rg] = *reinterpret_cast<const float4 *>(src);
+                        } else {
+                            if (i < a.m) c0v[cc][rg].x = src[0];
+                            if (i + 1 < a.m) c0v[cc][rg].y = src[1];
+                            if (i + 2 < a.m) c0v[cc][rg].z = src[2];
+                            if (i + 3 < a.m) c0v[cc][rg].w = src[3];
+                        }
                     }
                 }
-            }
 #pragma unroll
-            for (int cc = 0; cc < 4; ++cc) {
-                const int64_t jg = tile * W::BNT + c0 + h * 16 + cc;
-                if (jg >= a.n) continue;
+                for (int cc = 0; cc < 4; ++cc) {
+                    const int64_t jg = tile * W::BNT + c0 + h * 16 + cc;
+                    if (jg >= a.n) continue;
 #pragma unroll
-                for (int rg = 0; rg < 2; ++rg) {
-                    const int64_t i = i0 + r0 + rg * 32;
-                    const float4 x = acc.rows(rg, h * 4 + cc);
-                    const float4 o = axpby4(alpha, x, beta, c0v[cc][rg], use_c0);
-                    float *dst = C + i + jg * a.ldc;
-                    if (vec_c && i + 4 <= a.m) {
-                        *reinterpret_cast<float4 *>(dst) = o;
-                    } else {
-                        if (i < a.m) dst[0] = o.x;
-                        if (i + 1 < a.m) dst[1] = o.y;
-                        if (i + 2 < a.m) dst[2] = o.z;
-                        if (i + 3 < a.m) dst[3] = o.w;
+                    for (int rg = 0; rg < 2; ++rg) {
+                        const int64_t i = i0 + r0 + rg * 32;
+                        const float4 x = acc.rows(rg, h * 4 + cc);
+                        const float4 o = axpby4(alpha, x, beta, c0v[cc][rg], use_c0);
+                        float *dst = C + i + jg * a.ldc;
+                        if (vec_c && i + 4 <= a.m) {
+                            *reinterpret_cast<float4 *>(dst) = o;
+                        } else {
+                            if (i < a.m) dst[0] = o.x;
+                            if (i + 1 < a.m) dst[1] = o.y;
+                            if (i + 2 < a.m) dst[2] = o.z;
+                            if (i + 3 < a.m) dst[3] = o.w;
+                        }
                     }
                 }
             }

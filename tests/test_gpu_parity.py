@@ -306,3 +306,32 @@ def test_2048x2048x16_integer_matches_golden_fixture():
     A, B, C0 = gen(m, n, k, np.float32, "integer")
     C, _, _ = run(A, B, C0, fx["alpha"], fx["beta"])
     np.testing.assert_array_equal(C[fx["rows"]], np.array(fx["C_rows"], dtype=np.float32))
+
+
+@pytest.mark.parametrize("world", [2, 3])
+@pytest.mark.parametrize("m,n,k", [(4000, 64, 3000), (1000, 16, 20000), (3000, 200, 100)])
+def test_row_slabs_match_whole_problem_integer(world, m, n, k):
+    """The multi-GPU row split (bench.py --split rows) on one GPU: each slab of
+    rows [lo, hi) from bench.row_slab gets its own plan and runs on views of the
+    same A and C (lda = ldc = m, offset lo); together they must equal the whole
+    problem's execute and the oracle bit for bit (integer inputs: every partial
+    sum exact, whatever the slab's split of k)."""
+    import importlib.util
+    import os
+    spec = importlib.util.spec_from_file_location(
+        "bench", os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    A, B, C0 = gen(m, n, k, np.float32, "integer")
+    whole, pl, pb = run(A, B, C0, 1.5, 0.5)
+    dA = to_device(A)
+    dC = to_device(C0)
+    bm = pl.info()["bm"]
+    for r in range(world):
+        lo, hi = bench.row_slab(m, r, world, bm)
+        pl_r = tsmm.plan(hi - lo, n, k, torch.float32)
+        tsmm.execute(pl_r, 1.5, dA[lo:hi], pb, 0.5, dC[lo:hi])
+        pl_r.check()
+    split = dC.cpu().numpy()
+    np.testing.assert_array_equal(split, whole)
+    assert_parity(split, A, B, C0, 1.5, 0.5, exact=True)

@@ -400,48 +400,170 @@ __global__ void __launch_bounds__(TallCfg<T, NP>::THREADS, TallCfg<T, NP>::RESID
     tall_finish<T, NP>(red, a, slab, split, threadIdx.x, flag);
 }
 
-// Same decomposition without TMA: for A pointers or leading dimensions that a
-// tensor map cannot describe (not 16-byte aligned).  Plain guarded loads.
-template <typename T, int NP>
-__global__ void __launch_bounds__(TallCfg<T, NP>::CONSUMERS, 2)
-    tall_generic_kernel(const TallArgs a) {
-    using Cfg = TallCfg<T, NP>;
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    T *red = reinterpret_cast<T *>(smem_raw);
-    unsigned *flag = reinterpret_cast<unsigned *>(smem_raw + Cfg::RED * sizeof(T));
+// Same decomposition without TMA, for an A that a tensor map cannot describe
+// (its base or its column stride lda*sizeof(T) not a multiple of 16 bytes, as
+// for a column-major A with lda = m and m not a multiple of 4 -- most of a
+// random serving mix).  Stages of BM rows x BKS columns, as in the TMA kernel,
+// are copied by every thread with cp.async through a ring of S stages: the
+// copies of stage it + S - 1 are in flight while stage it is consumed, and one
+// __syncthreads per stage both publishes the landed stage and frees the one
+// consumed before it.  A column of A may start at any element address, so each
+// column is placed in shared memory at the same offset within 16 bytes (d
+// elements past a 16-byte boundary of its slot of BM + 16/sizeof(T) elements):
+// its 16-byte-aligned body then moves in 16-byte copies and only its head and
+// tail (under 16 bytes each) in element copies.  Consumers read the rows at
+// that offset with element loads.  Rows beyond m and columns beyond k are
+// zero-filled, as the tensor copy does; B's packed rows move in 16-byte
+// copies.  The thread tiles, reduction and split-K finish are the TMA
+// kernel's.  (Copies issued by all four consumer warps keep up with HBM; a
+// single producer warp issuing them, with the TMA kernel's mbarrier ring,
+// streamed at a quarter of the rate.)
+__device__ __forceinline__ void cp_async_elem(void *smem_dst, const void *gsrc, int bytes) {
+    if (bytes == 8)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_addr(smem_dst)), "l"(gsrc) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(smem_dst)), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_16(void *smem_dst, const void *gsrc) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(smem_dst)), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
 
-    const int warp = threadIdx.x / 32;
-    const int lane = threadIdx.x % 32;
+template <typename T, int NP>
+struct AsyncCfg {
+    using Cfg = TallCfg<T, NP>;
+    static constexpr int V = 16 / (int)sizeof(T);        // elements per 16 bytes
+    static constexpr int APAD = Cfg::BM + V;              // a column's slot
+    static constexpr int A_STAGE = Cfg::BKS * APAD;
+    static constexpr int STAGE_BYTES = (A_STAGE + Cfg::B_STAGE) * (int)sizeof(T);
+    // all the shared memory the resident blocks can have (228 KB per SM, 1 KB per block reserved)
+    static constexpr int BUDGET = Cfg::RESIDENT >= 3 ? 74 * 1024 : 112 * 1024;
+    static constexpr int STAGES_RAW = BUDGET / STAGE_BYTES;
+    static constexpr int STAGES = STAGES_RAW < 2 ? 2 : (STAGES_RAW > 6 ? 6 : STAGES_RAW);
+    static constexpr int RED_BYTES = Cfg::RED * (int)sizeof(T);
+    static constexpr int DATA_BYTES =
+        STAGES * STAGE_BYTES > RED_BYTES ? STAGES * STAGE_BYTES : RED_BYTES;
+    static constexpr int SMEM = DATA_BYTES + 16;
+    static constexpr int CHUNKS = Cfg::BM / V;            // 16-byte chunks of a full column
+    static_assert(Cfg::RESIDENT * (SMEM + 1024) <= 228 * 1024, "resident blocks per SM");
+};
+
+template <typename T, int NP>
+__global__ void __launch_bounds__(TallCfg<T, NP>::CONSUMERS, TallCfg<T, NP>::RESIDENT)
+    tall_async_kernel(const TallArgs a) {
+    using Cfg = TallCfg<T, NP>;
+    using AC = AsyncCfg<T, NP>;
+    constexpr int S = AC::STAGES;
+    constexpr int NT = Cfg::CONSUMERS;
+    constexpr int V = AC::V;
+    static_assert((Cfg::BKS * AC::CHUNKS) % NT == 0 && (Cfg::B_STAGE * (int)sizeof(T)) % 16 == 0, "stage split");
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    T *sA = reinterpret_cast<T *>(smem_raw);
+    T *sB = sA + S * AC::A_STAGE;
+    unsigned *flag = reinterpret_cast<unsigned *>(smem_raw + AC::DATA_BYTES);
+
+    const int tid = threadIdx.x;
+    const int warp = tid / 32;
+    const int lane = tid % 32;
     const int64_t slab = blockIdx.x;
     const int split = blockIdx.y;
     const int64_t k0 = (int64_t)split * a.kchunk;
-    const int64_t k1 = (k0 + a.kchunk < a.k) ? k0 + a.kchunk : a.k;
+    const int64_t k1 = (k0 + a.kchunk < a.kp) ? k0 + a.kchunk : a.kp;
+    const int iters = (int)((k1 - k0) / Cfg::BKS);
+    const int64_t i0 = slab * Cfg::BM;
+    const int rows = (int)((a.m - i0 < Cfg::BM) ? a.m - i0 : Cfg::BM);  // rows of this slab inside A
+    const T *A = static_cast<const T *>(a.A);
+    const T *Bp = static_cast<const T *>(a.Bp);
+    // offset within 16 bytes of element (i0, p): (d0 + p*lda) mod V
+    const int d0 = (int)(((reinterpret_cast<uintptr_t>(A) / sizeof(T)) + (uint64_t)i0) & (V - 1));
+    const int ldv = (int)((uint64_t)a.lda & (V - 1));
+    auto col_off = [&](int64_t p) { return (d0 + (int)((uint64_t)p & (V - 1)) * ldv) & (V - 1); };
+
+    // Column c's rows 0..rows-1 are written once each: the head (rows before the
+    // first 16-byte boundary) and the tail (rows after the last full chunk that
+    // ends inside A) by element copies, the full chunks in between by 16-byte
+    // copies; rows at or beyond `rows`, and columns at or beyond k, by zeros.
+    auto issue = [&](int st, int it) {
+        const int64_t kk = k0 + (int64_t)it * Cfg::BKS;
+        T *dA = sA + st * AC::A_STAGE;
+#pragma unroll 4
+        for (int j = 0; j < Cfg::BKS * AC::CHUNKS / NT; ++j) {
+            const int e = tid + NT * j;
+            const int c = e / AC::CHUNKS;
+            const int q = e % AC::CHUNKS;
+            const int64_t p = kk + c;
+            const int d = col_off(p);
+            const int r = ((V - d) & (V - 1)) + q * V;  // first row of this chunk
+            if (p < a.k && r + V <= rows) cp_async_16(dA + c * AC::APAD + d + r, A + (i0 + r) + p * a.lda);
+        }
+        for (int e = tid; e < Cfg::BKS * 2 * V; e += NT) {
+            const int c = e / (2 * V);
+            const int u = e % (2 * V);
+            const int64_t p = kk + c;
+            const int d = col_off(p);
+            const int head = (V - d) & (V - 1);
+            const int body_end = head + ((rows - head > 0 ? rows - head : 0) / V) * V;
+            const int r = u < V ? u : body_end + (u - V);
+            const bool mine = u < V ? (u < head) : (r < rows);
+            if (p < a.k && mine && r < rows)
+                cp_async_elem(dA + c * AC::APAD + d + r, A + (i0 + r) + p * a.lda, (int)sizeof(T));
+        }
+        if (rows < Cfg::BM || kk + Cfg::BKS > a.k) {  // the slab's or the k range's edge: zeros
+            for (int e = tid; e < Cfg::BKS * Cfg::BM; e += NT) {
+                const int c = e / Cfg::BM;
+                const int r = e % Cfg::BM;
+                const int64_t p = kk + c;
+                if (p >= a.k || r >= rows) dA[c * AC::APAD + col_off(p) + r] = T(0);
+            }
+        }
+        T *dB = sB + st * Cfg::B_STAGE;
+        const T *gB = Bp + kk * NP;
+        constexpr int BV16 = Cfg::B_STAGE * (int)sizeof(T) / 16;
+        for (int e = tid; e < BV16; e += NT)
+            cp_async_16(reinterpret_cast<char *>(dB) + 16 * e, reinterpret_cast<const char *>(gB) + 16 * e);
+    };
+
     const int wm = warp % Cfg::WM;
     const int wk = warp / Cfg::WM;
     const int g = lane / Cfg::LR;
     const int lr = lane % Cfg::LR;
     const int rloc = wm * Cfg::WROWS + lr * Cfg::RV;
     const int cloc = g * Cfg::CN;
-    const int64_t i0 = slab * Cfg::BM;
-    const T *A = static_cast<const T *>(a.A);
-    const T *Bp = static_cast<const T *>(a.Bp);
-
     typename TallAcc<T, NP>::type acc;
     acc.zero();
 
-    for (int64_t kb = k0; kb < k1; kb += Cfg::BKS) {
+#pragma unroll
+    for (int s = 0; s < S - 1; ++s) {
+        if (s < iters) issue(s, s);
+        cp_async_commit();
+    }
+    for (int it = 0; it < iters; ++it) {
+        cp_async_wait<S - 2>();  // this thread's copies of stage it have landed
+        __syncthreads();         // everyone's have; stage it - 1 is consumed by every warp
+        const int nxt = it + S - 1;
+        if (nxt < iters) issue(nxt % S, nxt);
+        cp_async_commit();
+        const int st = it % S;
+        const T *As = sA + st * AC::A_STAGE;
+        const T *Bs = sB + st * Cfg::B_STAGE;
+        const int64_t kk = k0 + (int64_t)it * Cfg::BKS;
+#pragma unroll
         for (int c = 0; c < Cfg::KPW; ++c) {
-            const int64_t p = kb + wk * Cfg::KPW + c;
-            if (p >= k1) break;
+            const int col = wk * Cfg::KPW + c;
+            const T *colp = As + col * AC::APAD + col_off(kk + col);
             Vec<T, Cfg::R> av;
 #pragma unroll
-            for (int r = 0; r < Cfg::R; ++r) {
-                const int64_t i = i0 + Cfg::row(rloc, r);
-                av.v[r] = (i < a.m) ? A[i + p * a.lda] : T(0);
-            }
-            acc.fma_column(av, Bp + p * NP + cloc);
+            for (int r = 0; r < Cfg::R; ++r) av.v[r] = colp[Cfg::row(rloc, r)];
+            acc.fma_column(av, Bs + col * NP + cloc);
         }
     }
+    cp_async_wait<0>();
+    __syncthreads();  // every warp is done with the ring: it becomes the reduction buffer
+    T *red = sA;
 #pragma unroll
     for (int c = 0; c < Cfg::CN; ++c) {
         Vec<T, Cfg::R> v;
@@ -450,7 +572,7 @@ __global__ void __launch_bounds__(TallCfg<T, NP>::CONSUMERS, 2)
         tall_store_rows<Cfg, T>(red + (wk * NP + cloc + c) * Cfg::BM, rloc, v);
     }
     named_barrier(1, Cfg::CONSUMERS);
-    tall_finish<T, NP>(red, a, slab, split, threadIdx.x, flag);
+    tall_finish<T, NP>(red, a, slab, split, tid, flag);
 }
 
 template <typename T, int NP>
@@ -467,16 +589,16 @@ cudaError_t launch_tall_tma_t(const CUtensorMap *tmap, const TallArgs &a, cudaSt
 }
 
 template <typename T, int NP>
-cudaError_t launch_tall_generic_t(const TallArgs &a, cudaStream_t s) {
+cudaError_t launch_tall_async_t(const TallArgs &a, cudaStream_t s) {
     using Cfg = TallCfg<T, NP>;
-    const int smem = Cfg::RED * (int)sizeof(T) + 16;
+    const int smem = AsyncCfg<T, NP>::SMEM;
     {
         const cudaError_t e =
-            ensure_smem_limit(reinterpret_cast<const void *>(tall_generic_kernel<T, NP>), smem);
+            ensure_smem_limit(reinterpret_cast<const void *>(tall_async_kernel<T, NP>), smem);
         if (e != cudaSuccess) return e;
     }
     dim3 grid((unsigned)a.slabs, (unsigned)a.splits);
-    tall_generic_kernel<T, NP><<<grid, Cfg::CONSUMERS, smem, s>>>(a);
+    tall_async_kernel<T, NP><<<grid, Cfg::CONSUMERS, smem, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -486,7 +608,7 @@ cudaError_t launch_tall_dispatch(bool tma, int np, const CUtensorMap *tmap, cons
 #define TSMM_TALL_CASE(NPV)                                                       \
     case NPV:                                                                     \
         return tma ? launch_tall_tma_t<T, NPV>(tmap, a, s)                        \
-                   : launch_tall_generic_t<T, NPV>(a, s);
+                   : launch_tall_async_t<T, NPV>(a, s);
     switch (np) {
         TSMM_TALL_CASE(1)
         TSMM_TALL_CASE(2)

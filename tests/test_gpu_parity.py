@@ -120,6 +120,23 @@ def test_unaligned_integer_matches_tma_bitwise(dtype):
     assert_parity(C_tma, A, B, C0, 1.5, 0.5, exact=True)
 
 
+@pytest.mark.parametrize("dtype", DT)
+@pytest.mark.parametrize("n", [1, 5, 16, 24, 40, 64])
+@pytest.mark.parametrize("m,k,lda_pad,a_off", [(1027, 333, 1, 0), (1026, 700, 2, 1), (2049, 3001, 3, 3),
+                                               (257, 40, 0, 2), (513, 20000, 1, 1)])
+def test_unaligned_A_every_offset_integer_exact(dtype, n, m, k, lda_pad, a_off):
+    """A whose column stride or base is not 16-byte aligned streams through the
+    cp.async kernel, which places each column at its own offset within 16
+    bytes: every offset (a_off 0..3, lda = m + 1..3), a ragged last slab, k not a
+    multiple of 32, and split-K (k = 20000).  Integer inputs: equal to the TMA
+    path bit for bit and to the oracle."""
+    A, B, C0 = gen(m, n, k, dtype, "integer")
+    C_tma, _, _ = run(A, B, C0, 1.5, 0.5, lda=m + (4 - m % 4) % 4)
+    C_un, _, _ = run(A, B, C0, 1.5, 0.5, lda=m + lda_pad, a_offset=a_off)
+    np.testing.assert_array_equal(C_un, C_tma)
+    assert_parity(C_un, A, B, C0, 1.5, 0.5, exact=True)
+
+
 # ------------------------------------------------------------- special cases
 @pytest.mark.parametrize("dtype", DT)
 @pytest.mark.parametrize("n,k", [(16, 100), (200, 64)])

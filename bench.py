@@ -75,6 +75,9 @@ def parse():
     p.add_argument("--only", type=int, default=None,
                    help="profiling/small runs: keep only this n (tall) or k (rankk)")
     p.add_argument("--beta", type=float, default=None, help="profiling/small runs: one beta only")
+    p.add_argument("--lda-pad", type=int, default=0,
+                   help="store A with lda = m + PAD (PAD not a multiple of 16/element size: the path "
+                        "for an A that a tensor map cannot describe)")
     p.add_argument("--split", choices=["replicas", "rows"], default="replicas",
                    help="N > 1: independent replicas (weak scaling) or one problem's rows split over ranks")
     p.add_argument("--no-e2e", action="store_true")
@@ -106,13 +109,14 @@ def workload_points(args):
 
 
 def workload_name(args):
+    pad = f", A stored with lda = m + {args.lda_pad}" if getattr(args, "lda_pad", 0) else ""
     if args.size or args.only or args.beta is not None:
         return "reduced case for profiling: " + ", ".join(
-            f"m={m} n={n} k={k} beta={b}" for (m, n, k, b) in workload_points(args))
+            f"m={m} n={n} k={k} beta={b}" for (m, n, k, b) in workload_points(args)) + pad
     if args.workload == "tall":
         mode = "" if args.precision == "native" else " in the BF16x3 tensor-core mode"
         return (f"memory-bound sweep {args.dtype.upper()} m=k=32768, n in {SWEEP_N}, "
-                f"beta in {{0,1}}, alpha=1, B pre-packed and reused{mode}")
+                f"beta in {{0,1}}, alpha=1, B pre-packed and reused{mode}{pad}")
     return f"rank-k {args.dtype.upper()} m=n=16384, k in {RANKK_K}, beta=1, B pre-packed"
 
 
@@ -396,7 +400,7 @@ def measure_fp_peaks(tsmm):
 
 
 def time_points(tsmm, torch, pts, tdt, steps, warmup, precision=0, world=1, rank=0, split="replicas",
-                sampler=None):
+                sampler=None, lda_pad=0):
     """Resident inputs for every point (one A per distinct (m, k), B packed once
     per (n, k), C0 per point), `warmup` untimed steps, then `steps` timed steps
     with CUDA events around each launch on the launching stream.  With split =
@@ -407,15 +411,15 @@ def time_points(tsmm, torch, pts, tdt, steps, warmup, precision=0, world=1, rank
 
     stream = torch.cuda.current_stream()
 
-    def dmat(rows, cols, seed):
-        t = torch.empty((cols, rows), dtype=tdt, device="cuda")
+    def dmat(rows, cols, seed, pad=0):
+        t = torch.empty((cols, rows + pad), dtype=tdt, device="cuda")
         ti.fill_torch(t, seed, "uniform")
-        return t.t()
+        return t.t()[:rows]
 
     A, packed, plans, C, pack_ms, slab = {}, {}, {}, {}, {}, {}
     for (m, n, k, beta) in pts:
         if (m, k) not in A:
-            A[(m, k)] = dmat(m, k, ti.SEED_A)
+            A[(m, k)] = dmat(m, k, ti.SEED_A, lda_pad)
     for (m, n, k, beta) in pts:
         if (n, k) not in packed:
             Bsrc = dmat(k, n, ti.SEED_B)
@@ -548,7 +552,7 @@ def run_ours(args):
 
     sampler = ClockSampler(local)
     points, elapsed_ms, launches, st = time_points(tsmm, torch, pts, tdt, args.steps, args.warmup, prec, world,
-                                                   rank, args.split, sampler)
+                                                   rank, args.split, sampler, args.lda_pad)
     clocks = st["clocks"]
     step_flops = sum(flops(p["rows"][1] - p["rows"][0], p["n"], p["k"]) for p in points)
     if args.split == "rows":
@@ -580,7 +584,7 @@ def run_ours(args):
 
     # ---------------- end to end: host buffers, copies inside the timed region
     e2e = None
-    if not args.no_e2e and args.split == "replicas":
+    if not args.no_e2e and args.split == "replicas" and not args.lda_pad:
         e2e = run_e2e(args, tsmm, torch, tdt, es, pts, st["A"], st["packed"], st["plans"], world)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -608,7 +612,8 @@ def run_ours(args):
     if cpu is not None:
         line["cpu_baseline"] = cpu
     if (rank == 0 and world == 1 and not args.no_extras and args.workload == "tall" and args.dtype == "f32"
-            and args.precision == "native" and not (args.size or args.only or args.beta is not None)):
+            and args.precision == "native" and not (args.size or args.only or args.beta is not None)
+            and not args.lda_pad):
         line.update(run_extras(args, tsmm, torch, peaks, hbm_peak))
     if rank == 0:
         print(json.dumps(line))

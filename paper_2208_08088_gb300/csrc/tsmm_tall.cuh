@@ -400,44 +400,50 @@ __global__ void __launch_bounds__(TallCfg<T, NP>::THREADS, TallCfg<T, NP>::RESID
     tall_finish<T, NP>(red, a, slab, split, threadIdx.x, flag);
 }
 
-// Same decomposition without TMA, for an A that a tensor map cannot describe
+// Same decomposition without a tensor map, for an A that one cannot describe
 // (its base or its column stride lda*sizeof(T) not a multiple of 16 bytes, as
 // for a column-major A with lda = m and m not a multiple of 4 -- most of a
-// random serving mix).  Stages of BM rows x BKS columns, as in the TMA kernel,
-// are copied by every thread with cp.async through a ring of S stages: the
-// copies of stage it + S - 1 are in flight while stage it is consumed, and one
-// __syncthreads per stage both publishes the landed stage and frees the one
-// consumed before it.  A column of A may start at any element address, so each
-// column is placed in shared memory at the same offset within 16 bytes (d
-// elements past a 16-byte boundary of its slot of BM + 16/sizeof(T) elements):
-// its 16-byte-aligned body then moves in 16-byte copies and only its head and
-// tail (under 16 bytes each) in element copies.  Consumers read the rows at
-// that offset with element loads.  Rows beyond m and columns beyond k are
-// zero-filled, as the tensor copy does; B's packed rows move in 16-byte
-// copies.  The thread tiles, reduction and split-K finish are the TMA
-// kernel's.  (Copies issued by all four consumer warps keep up with HBM; a
-// single producer warp issuing them, with the TMA kernel's mbarrier ring,
-// streamed at a quarter of the rate.)
-__device__ __forceinline__ void cp_async_elem(void *smem_dst, const void *gsrc, int bytes) {
+// random serving mix).  The structure is the TMA kernel's: consumer warps, a
+// producer warp and a ring of mbarrier-guarded stages of BM rows x BKS columns.
+// Each of the producer's 32 lanes moves one column of a stage: a column of A
+// may start at any element address, so it is placed in shared memory at its
+// own offset within 16 bytes (d elements into its slot), its 16-byte-aligned
+// interior moves in one bulk copy (cp.async.bulk, the copy engine of the
+// tensor copy, counted on the stage's barrier in bytes), and its head and tail
+// (under 16 bytes each) by element cp.async copies, whose completion the
+// lane's arrival on the barrier waits for (cp.async.mbarrier.arrive.noinc), so
+// no lane waits on a load; nothing outside the column's rows of A is read.
+// Columns beyond k are zero-filled by copies with a zero source size; rows
+// beyond m are left as they are (their results are never stored).  Consumers
+// read the rows at the column's offset with element loads.  B's packed rows
+// come in one bulk copy per stage.  The thread tiles, reduction and split-K
+// finish are the TMA kernel's.
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.expect_tx.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+// Element copy global -> shared; a zero source size writes zeros and reads nothing.
+__device__ __forceinline__ void cp_async_elem(void *smem_dst, const void *gsrc, bool valid, int bytes) {
+    const uint32_t n = valid ? (uint32_t)bytes : 0u;
     if (bytes == 8)
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_addr(smem_dst)), "l"(gsrc) : "memory");
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(smem_addr(smem_dst)), "l"(gsrc), "r"(n)
+                     : "memory");
     else
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(smem_dst)), "l"(gsrc) : "memory");
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(smem_addr(smem_dst)), "l"(gsrc), "r"(n)
+                     : "memory");
 }
-__device__ __forceinline__ void cp_async_16(void *smem_dst, const void *gsrc) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(smem_dst)), "l"(gsrc) : "memory");
+__device__ __forceinline__ void cp_async_zero16(void *smem_dst, const void *gsrc) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, 0;" ::"r"(smem_addr(smem_dst)), "l"(gsrc) : "memory");
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+// The barrier counts this thread's arrival once all its earlier cp.async copies have landed.
+__device__ __forceinline__ void cp_async_arrive_noinc(uint64_t *bar) {
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
 
 template <typename T, int NP>
 struct AsyncCfg {
     using Cfg = TallCfg<T, NP>;
     static constexpr int V = 16 / (int)sizeof(T);        // elements per 16 bytes
-    static constexpr int APAD = Cfg::BM + V;              // a column's slot
+    static constexpr int APAD = Cfg::BM + 2 * V;          // a column's slot: offset + rows + the tail chunk
     static constexpr int A_STAGE = Cfg::BKS * APAD;
     static constexpr int STAGE_BYTES = (A_STAGE + Cfg::B_STAGE) * (int)sizeof(T);
     // all the shared memory the resident blocks can have (228 KB per SM, 1 KB per block reserved)
@@ -447,28 +453,28 @@ struct AsyncCfg {
     static constexpr int RED_BYTES = Cfg::RED * (int)sizeof(T);
     static constexpr int DATA_BYTES =
         STAGES * STAGE_BYTES > RED_BYTES ? STAGES * STAGE_BYTES : RED_BYTES;
-    static constexpr int SMEM = DATA_BYTES + 16;
-    static constexpr int CHUNKS = Cfg::BM / V;            // 16-byte chunks of a full column
+    static constexpr int SMEM = DATA_BYTES + 2 * STAGES * 8 + 16;
+    static_assert(Cfg::BKS == 32, "one producer lane per column");
     static_assert(Cfg::RESIDENT * (SMEM + 1024) <= 228 * 1024, "resident blocks per SM");
 };
 
 template <typename T, int NP>
-__global__ void __launch_bounds__(TallCfg<T, NP>::CONSUMERS, TallCfg<T, NP>::RESIDENT)
+__global__ void __launch_bounds__(TallCfg<T, NP>::THREADS, TallCfg<T, NP>::RESIDENT)
     tall_async_kernel(const TallArgs a) {
     using Cfg = TallCfg<T, NP>;
     using AC = AsyncCfg<T, NP>;
     constexpr int S = AC::STAGES;
-    constexpr int NT = Cfg::CONSUMERS;
     constexpr int V = AC::V;
-    static_assert((Cfg::BKS * AC::CHUNKS) % NT == 0 && (Cfg::B_STAGE * (int)sizeof(T)) % 16 == 0, "stage split");
     extern __shared__ __align__(128) unsigned char smem_raw[];
     T *sA = reinterpret_cast<T *>(smem_raw);
     T *sB = sA + S * AC::A_STAGE;
-    unsigned *flag = reinterpret_cast<unsigned *>(smem_raw + AC::DATA_BYTES);
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem_raw + AC::DATA_BYTES);
+    uint64_t *empty = full + S;
+    unsigned *flag = reinterpret_cast<unsigned *>(empty + S);
+    unsigned *abort_flag = flag + 1;
 
-    const int tid = threadIdx.x;
-    const int warp = tid / 32;
-    const int lane = tid % 32;
+    const int warp = threadIdx.x / 32;
+    const int lane = threadIdx.x % 32;
     const int64_t slab = blockIdx.x;
     const int split = blockIdx.y;
     const int64_t k0 = (int64_t)split * a.kchunk;
@@ -477,56 +483,70 @@ __global__ void __launch_bounds__(TallCfg<T, NP>::CONSUMERS, TallCfg<T, NP>::RES
     const int64_t i0 = slab * Cfg::BM;
     const int rows = (int)((a.m - i0 < Cfg::BM) ? a.m - i0 : Cfg::BM);  // rows of this slab inside A
     const T *A = static_cast<const T *>(a.A);
-    const T *Bp = static_cast<const T *>(a.Bp);
     // offset within 16 bytes of element (i0, p): (d0 + p*lda) mod V
     const int d0 = (int)(((reinterpret_cast<uintptr_t>(A) / sizeof(T)) + (uint64_t)i0) & (V - 1));
     const int ldv = (int)((uint64_t)a.lda & (V - 1));
     auto col_off = [&](int64_t p) { return (d0 + (int)((uint64_t)p & (V - 1)) * ldv) & (V - 1); };
 
-    // Column c's rows 0..rows-1 are written once each: the head (rows before the
-    // first 16-byte boundary) and the tail (rows after the last full chunk that
-    // ends inside A) by element copies, the full chunks in between by 16-byte
-    // copies; rows at or beyond `rows`, and columns at or beyond k, by zeros.
-    auto issue = [&](int st, int it) {
-        const int64_t kk = k0 + (int64_t)it * Cfg::BKS;
-        T *dA = sA + st * AC::A_STAGE;
-#pragma unroll 4
-        for (int j = 0; j < Cfg::BKS * AC::CHUNKS / NT; ++j) {
-            const int e = tid + NT * j;
-            const int c = e / AC::CHUNKS;
-            const int q = e % AC::CHUNKS;
-            const int64_t p = kk + c;
-            const int d = col_off(p);
-            const int r = ((V - d) & (V - 1)) + q * V;  // first row of this chunk
-            if (p < a.k && r + V <= rows) cp_async_16(dA + c * AC::APAD + d + r, A + (i0 + r) + p * a.lda);
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&full[s], 32);  // the producer warp's lanes
+            mbar_init(&empty[s], Cfg::NWARPS);
         }
-        for (int e = tid; e < Cfg::BKS * 2 * V; e += NT) {
-            const int c = e / (2 * V);
-            const int u = e % (2 * V);
-            const int64_t p = kk + c;
-            const int d = col_off(p);
-            const int head = (V - d) & (V - 1);
-            const int body_end = head + ((rows - head > 0 ? rows - head : 0) / V) * V;
-            const int r = u < V ? u : body_end + (u - V);
-            const bool mine = u < V ? (u < head) : (r < rows);
-            if (p < a.k && mine && r < rows)
-                cp_async_elem(dA + c * AC::APAD + d + r, A + (i0 + r) + p * a.lda, (int)sizeof(T));
-        }
-        if (rows < Cfg::BM || kk + Cfg::BKS > a.k) {  // the slab's or the k range's edge: zeros
-            for (int e = tid; e < Cfg::BKS * Cfg::BM; e += NT) {
-                const int c = e / Cfg::BM;
-                const int r = e % Cfg::BM;
-                const int64_t p = kk + c;
-                if (p >= a.k || r >= rows) dA[c * AC::APAD + col_off(p) + r] = T(0);
-            }
-        }
-        T *dB = sB + st * Cfg::B_STAGE;
-        const T *gB = Bp + kk * NP;
-        constexpr int BV16 = Cfg::B_STAGE * (int)sizeof(T) / 16;
-        for (int e = tid; e < BV16; e += NT)
-            cp_async_16(reinterpret_cast<char *>(dB) + 16 * e, reinterpret_cast<const char *>(gB) + 16 * e);
-    };
+        *abort_flag = 0u;
+        fence_mbar_init();
+    }
+    __syncthreads();
 
+    if (warp == Cfg::NWARPS) {
+        // ---------------- producer warp: lane c moves column c of each stage
+        const uint64_t pol_a = policy_evict_first();
+        const uint64_t pol_b = policy_evict_last();
+        const T *Bp = static_cast<const T *>(a.Bp);
+        for (int it = 0; it < iters; ++it) {
+            const int st = it % S;
+            if (it >= S) {
+                const bool got = mbar_wait_bounded(&empty[st], ((it / S) & 1) ^ 1);
+                if (!__all_sync(0xffffffffu, got)) {
+                    if (lane == 0) atomicOr(a.status, kDevErrTimeout);
+                    break;
+                }
+            }
+            const int64_t kk = k0 + (int64_t)it * Cfg::BKS;
+            const int64_t p = kk + lane;
+            const int d = col_off(p);
+            T *slot = sA + st * AC::A_STAGE + lane * AC::APAD + d;  // row r at slot[r]
+            if (lane == 0) {
+                mbar_expect_tx(&full[st], Cfg::B_STAGE * (int)sizeof(T));
+                bulk_load(sB + st * Cfg::B_STAGE, Bp + kk * NP, Cfg::B_STAGE * (int)sizeof(T), &full[st], pol_b);
+            }
+            if (p < a.k) {
+                const T *col = A + i0 + p * a.lda;
+                const int head = (V - d) & (V - 1);        // rows before the first 16-byte boundary
+                const int h = head < rows ? head : rows;
+                const int nb = (rows - h) / V;              // whole 16-byte chunks inside the rows
+                const int tail0 = h + nb * V;
+                if (nb > 0) {
+                    mbar_expect_tx(&full[st], (uint32_t)(nb * 16));
+                    bulk_load(slot + h, col + h, (uint32_t)(nb * 16), &full[st], pol_a);
+                }
+#pragma unroll
+                for (int r = 0; r < V; ++r)
+                    if (r < h) cp_async_elem(slot + r, col + r, true, (int)sizeof(T));
+#pragma unroll
+                for (int r = 0; r < V; ++r)
+                    if (tail0 + r < rows) cp_async_elem(slot + tail0 + r, col + tail0 + r, true, (int)sizeof(T));
+            } else {
+                // beyond k: zeros, as B's padding (the whole slot, 16 bytes at a time)
+                T *slot0 = sA + st * AC::A_STAGE + lane * AC::APAD;
+                for (int r = 0; r < AC::APAD; r += V) cp_async_zero16(slot0 + r, Bp);  // 16-byte aligned source, not read
+            }
+            cp_async_arrive_noinc(&full[st]);  // this lane's arrival, once its element copies have landed
+        }
+        return;
+    }
+
+    // ---------------- consumer warps
     const int wm = warp % Cfg::WM;
     const int wk = warp / Cfg::WM;
     const int g = lane / Cfg::LR;
@@ -536,18 +556,13 @@ __global__ void __launch_bounds__(TallCfg<T, NP>::CONSUMERS, TallCfg<T, NP>::RES
     typename TallAcc<T, NP>::type acc;
     acc.zero();
 
-#pragma unroll
-    for (int s = 0; s < S - 1; ++s) {
-        if (s < iters) issue(s, s);
-        cp_async_commit();
-    }
+    bool ok = true;
     for (int it = 0; it < iters; ++it) {
-        cp_async_wait<S - 2>();  // this thread's copies of stage it have landed
-        __syncthreads();         // everyone's have; stage it - 1 is consumed by every warp
-        const int nxt = it + S - 1;
-        if (nxt < iters) issue(nxt % S, nxt);
-        cp_async_commit();
         const int st = it % S;
+        if (!mbar_wait_bounded(&full[st], (it / S) & 1)) {
+            ok = false;
+            break;
+        }
         const T *As = sA + st * AC::A_STAGE;
         const T *Bs = sB + st * Cfg::B_STAGE;
         const int64_t kk = k0 + (int64_t)it * Cfg::BKS;
@@ -560,9 +575,16 @@ __global__ void __launch_bounds__(TallCfg<T, NP>::CONSUMERS, TallCfg<T, NP>::RES
             for (int r = 0; r < Cfg::R; ++r) av.v[r] = colp[Cfg::row(rloc, r)];
             acc.fma_column(av, Bs + col * NP + cloc);
         }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[st]);
     }
-    cp_async_wait<0>();
-    __syncthreads();  // every warp is done with the ring: it becomes the reduction buffer
+    if (!ok && lane == 0) {
+        atomicOr(a.status, kDevErrTimeout);
+        atomicOr(abort_flag, 1u);
+    }
+    // every consumer warp gets here (each wait above is bounded)
+    named_barrier(1, Cfg::CONSUMERS);
+    if (*abort_flag != 0u) return;  // tile not written; the host sees TSMM_ERR_TIMEOUT
     T *red = sA;
 #pragma unroll
     for (int c = 0; c < Cfg::CN; ++c) {
@@ -572,7 +594,7 @@ __global__ void __launch_bounds__(TallCfg<T, NP>::CONSUMERS, TallCfg<T, NP>::RES
         tall_store_rows<Cfg, T>(red + (wk * NP + cloc + c) * Cfg::BM, rloc, v);
     }
     named_barrier(1, Cfg::CONSUMERS);
-    tall_finish<T, NP>(red, a, slab, split, tid, flag);
+    tall_finish<T, NP>(red, a, slab, split, threadIdx.x, flag);
 }
 
 template <typename T, int NP>
@@ -598,7 +620,7 @@ cudaError_t launch_tall_async_t(const TallArgs &a, cudaStream_t s) {
         if (e != cudaSuccess) return e;
     }
     dim3 grid((unsigned)a.slabs, (unsigned)a.splits);
-    tall_async_kernel<T, NP><<<grid, Cfg::CONSUMERS, smem, s>>>(a);
+    tall_async_kernel<T, NP><<<grid, Cfg::THREADS, smem, s>>>(a);
     return cudaGetLastError();
 }
 

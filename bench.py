@@ -874,7 +874,7 @@ def serving_session(args, tsmm, torch, N, load, num_streams):
     [64, 8192], n log-uniform in [1, 64], drawn once from a seed); requests pick a
     B uniformly and m log-uniform in [1024, 262144]; FP32, alpha = 1, every third
     request with beta = 1 (reads its C0), the others beta = 0.  The server admits
-    under a 40 GB budget and batches continuously (grouped persistent launches on
+    under a 40 GB budget and batches continuously (grouped launches, one block per work item, on
     `num_streams` lanes).  Capacity is measured with every request arriving at
     once; then Poisson arrivals at `load` x capacity give the p50 / p90 / p99
     arrival-to-completion latency and the aggregate GFLOP/s.
@@ -974,7 +974,7 @@ def serving_session(args, tsmm, torch, N, load, num_streams):
     return {"workload": f"{N} FP32 TSMM requests, Poisson arrivals at {load:.2f} x measured capacity, "
                         "m log-uniform [1024, 262144], 32 resident packed B with k log-uniform [64, 8192], "
                         "n log-uniform [1, 64], beta = 1 for every third request; 40 GB admission budget; "
-                        f"grouped persistent launches on {num_streams} lanes",
+                        f"grouped launches (one block per work item) on {num_streams} lanes",
             "gflops": round(fl.sum() / span / 1e9, 1), "span_ms": round(span * 1e3, 2),
             "total_gflop": round(fl.sum() / 1e9, 1),
             "latency_ms": {"p50": round(float(np.percentile(lat, 50)) * 1e3, 3),

@@ -239,13 +239,14 @@ typedef struct tsmm_group_item {
  * tsmm_execute_grouped -- run `count` independent TSMMs (uneven shapes, each
  * with its own plan, packed B, alpha, beta, A and C) with as few kernel
  * launches as possible: the grouped execution of many pre-packed products that
- * the paper's reuse argument (Section III) motivates.  Regime (i) problems
- * whose A is 16-byte aligned with lda*sizeof(element) a multiple of 16 are
- * batched per (dtype, padded column count) into launches of one persistent
- * kernel, at most 48 problems per launch, whose blocks walk the problems' work
- * items (m-slab x k-split) and keep their TMA pipeline running across item
- * boundaries; any other problem runs as its own tsmm_execute launch on the same
- * stream.  Results equal tsmm_execute's bit for bit.  Every item is validated
+ * the paper's reuse argument (Section III) motivates.  Regime (i) problems in
+ * the native precision are batched per (dtype, padded column count, whether
+ * a tensor map can describe A: base 16-byte aligned and lda*sizeof(element) a
+ * multiple of 16) into launches of one grouped kernel, at most 48 problems per
+ * launch, with one thread block per work item (m-slab x k-split) of every
+ * problem, so that items of unequal cost share the GPU as its block scheduler
+ * hands out SMs; any other problem runs as its own tsmm_execute launch on the
+ * same stream.  Results equal tsmm_execute's bit for bit.  Every item is validated
  * as tsmm_execute would before anything is launched; two items may not share a
  * plan (INVALID_ARG), since a plan's split-K workspace serves one problem at a
  * time.  Asynchronous on `stream`.
@@ -304,10 +305,10 @@ TSMM_API int64_t tsmm_plan_cache_size(void);
  * that alone holds at least the bytes of the current one (and 256 MiB), so a
  * small request completes with its sub-batch, not with a much larger request.  A
  * lane is three high-priority streams and one low-priority stream: the first
- * sub-batch runs as persistent grouped launches, one per kernel class, spread
- * over the high-priority streams; the others run one thread block per work
- * item on the low-priority stream, so newly launched small work gets SMs as
- * items finish.
+ * sub-batch runs as grouped launches, one per kernel class, spread over the
+ * high-priority streams; the others run on the low-priority stream.  Every
+ * grouped launch has one thread block per work item, so newly launched small
+ * work gets SMs as items finish.
  * Each request's plan depends only on its shape, so its result is the same bit
  * for bit alone or in any mix.  The caller owns A, C and the packed B, and must
  * keep them alive until the request's completion has been polled.

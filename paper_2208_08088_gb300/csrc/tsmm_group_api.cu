@@ -1,9 +1,10 @@
 // tsmm_execute_grouped: many pre-packed TSMMs in as few launches as possible.
-// Regime (i) problems whose A a tensor map can describe are batched, per dtype
-// and padded column count, into launches of the grouped persistent kernel (up
-// to kGroupMax problems each); every other problem (regime (ii), alpha = 0,
-// k = 0, unaligned A) is executed by its own tsmm_execute launch on the same
-// stream.
+// Regime (i) problems are batched, per dtype, padded column count and kind of
+// A (one a tensor map can describe, or one whose base or column stride is not
+// a multiple of 16 bytes), into launches of the grouped kernel (up to
+// kGroupMax problems and INT_MAX work items each, one block per item); every
+// other problem (regime (ii), alpha = 0, k = 0, the BF16x3 mode) is executed by
+// its own tsmm_execute launch on the same stream.
 #include <cudaTypedefs.h>
 
 #include <algorithm>
@@ -11,14 +12,15 @@
 #include <map>
 #include <memory>
 #include <set>
+#include <tuple>
 #include <utility>
 #include <vector>
 
 #include "tsmm_group.cuh"
 
 namespace tsmm {
-cudaError_t launch_grouped_f32(int np, const GroupParams &gp, int num_sms, bool persistent, cudaStream_t s);
-cudaError_t launch_grouped_f64(int np, const GroupParams &gp, int num_sms, bool persistent, cudaStream_t s);
+cudaError_t launch_grouped_f32(int np, bool unaligned, const GroupParams &gp, cudaStream_t s);
+cudaError_t launch_grouped_f64(int np, bool unaligned, const GroupParams &gp, cudaStream_t s);
 }  // namespace tsmm
 
 using namespace tsmm;
@@ -61,20 +63,25 @@ tsmm_status validate(const tsmm_group_item &it) {
     return TSMM_OK;
 }
 
-bool groupable(const tsmm_group_item &it) {
+// 0: not groupable (its own tsmm_execute launch); 1: A described by a tensor
+// map; 2: A whose base or column stride is not 16-byte aligned (element copies
+// of heads and tails, bulk copies of the rest).
+int group_kind(const tsmm_group_item &it) {
     tsmm_plan_t p = it.plan;
     const size_t es = dtype_size(p->dtype);
     const bool alpha_zero = it.alpha == 0.0 ||
                             (p->dtype == TSMM_F32 && static_cast<float>(it.alpha) == 0.0f);
-    return p->regime == 1 && p->precision == TSMM_PREC_NATIVE && p->m > 0 && p->n > 0 && p->k > 0 && !alpha_zero &&
-           is_aligned(it.A_dev, 16) && (it.lda * (int64_t)es) % 16 == 0 && p->m < INT_MAX &&
-           p->k < INT_MAX && (it.lda * (int64_t)es) < (1LL << 40) && encoder_grouped() != nullptr;
+    if (!(p->regime == 1 && p->precision == TSMM_PREC_NATIVE && p->m > 0 && p->n > 0 && p->k > 0 && !alpha_zero &&
+          p->m < INT_MAX && p->k < INT_MAX && p->slabs * (int64_t)p->splits < INT_MAX))
+        return 0;
+    const bool tma = is_aligned(it.A_dev, 16) && (it.lda * (int64_t)es) % 16 == 0 &&
+                     (it.lda * (int64_t)es) < (1LL << 40) && encoder_grouped() != nullptr;
+    return tma ? 1 : 2;
 }
 
 }  // namespace
 
-tsmm_status tsmm::execute_grouped(const tsmm_group_item *items, int count, tsmm_stream_t stream,
-                                  bool persistent) {
+tsmm_status tsmm::execute_grouped(const tsmm_group_item *items, int count, tsmm_stream_t stream) {
     if (count < 0 || (count > 0 && !items)) return TSMM_ERR_INVALID_ARG;
     std::set<tsmm_plan_t> seen;
     for (int i = 0; i < count; ++i) {
@@ -83,11 +90,12 @@ tsmm_status tsmm::execute_grouped(const tsmm_group_item *items, int count, tsmm_
         if (!seen.insert(items[i].plan).second) return TSMM_ERR_INVALID_ARG;  // shared workspace
     }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    // classes of groupable problems: (dtype, np) -> item indices
-    std::map<std::pair<int, int>, std::vector<int>> classes;
+    // classes of groupable problems: (dtype, np, kind of A) -> item indices
+    std::map<std::tuple<int, int, int>, std::vector<int>> classes;
     for (int i = 0; i < count; ++i) {
-        if (groupable(items[i])) {
-            classes[{(int)items[i].plan->dtype, items[i].plan->np}].push_back(i);
+        const int kind = group_kind(items[i]);
+        if (kind != 0) {
+            classes[std::make_tuple((int)items[i].plan->dtype, items[i].plan->np, kind)].push_back(i);
         } else {
             tsmm_status st = tsmm_execute(items[i].plan, items[i].alpha, items[i].A_dev, items[i].lda,
                                           items[i].pb, items[i].beta, items[i].C_dev, items[i].ldc,
@@ -98,24 +106,27 @@ tsmm_status tsmm::execute_grouped(const tsmm_group_item *items, int count, tsmm_
     std::unique_ptr<GroupParams> gp(new (std::nothrow) GroupParams());
     if (!gp) return TSMM_ERR_OUT_OF_MEMORY;
     for (auto &cls : classes) {
-        const tsmm_dtype dt = (tsmm_dtype)cls.first.first;
-        const int np = cls.first.second;
+        const tsmm_dtype dt = (tsmm_dtype)std::get<0>(cls.first);
+        const int np = std::get<1>(cls.first);
+        const bool unaligned = std::get<2>(cls.first) == 2;
         const std::vector<int> &idx = cls.second;
-        for (size_t c0 = 0; c0 < idx.size(); c0 += kGroupMax) {
-            const size_t c1 = std::min(idx.size(), c0 + kGroupMax);
+        // launches of at most kGroupMax problems and INT_MAX work items
+        size_t q = 0;
+        while (q < idx.size()) {
             int64_t total = 0;
-            int num_sms = 0;
             gp->count = 0;
-            for (size_t q = c0; q < c1; ++q) {
+            for (; q < idx.size() && gp->count < kGroupMax; ++q) {
                 const tsmm_group_item &it = items[idx[q]];
                 tsmm_plan_t p = it.plan;
+                const int64_t n_items = p->slabs * (int64_t)p->splits;
+                if (total + n_items > INT_MAX) break;  // n_items < INT_MAX: the next launch takes it
                 GroupProblem &g = gp->p[gp->count++];
                 const size_t es = dtype_size(dt);
                 const cuuint64_t gdim[2] = {(cuuint64_t)p->m, (cuuint64_t)p->k};
                 const cuuint64_t gstride[1] = {(cuuint64_t)(it.lda * (int64_t)es)};
                 const cuuint32_t box[2] = {(cuuint32_t)p->bm, (cuuint32_t)kTallBKS};
                 const cuuint32_t estr[2] = {1, 1};
-                if (encoder_grouped()(&g.tmA,
+                if (!unaligned && encoder_grouped()(&g.tmA,
                                       dt == TSMM_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
                                                      : CU_TENSOR_MAP_DATA_TYPE_FLOAT64,
                                       2, const_cast<void *>(it.A_dev), gdim, gstride, box, estr,
@@ -142,12 +153,11 @@ tsmm_status tsmm::execute_grouped(const tsmm_group_item *items, int count, tsmm_
                 a.kp = p->kp;
                 a.slabs = p->slabs;
                 g.item_begin = total;
-                total += p->slabs * p->splits;
-                num_sms = p->num_sms;
+                total += n_items;
             }
             gp->total_items = total;
-            cudaError_t e = dt == TSMM_F32 ? launch_grouped_f32(np, *gp, num_sms, persistent, s)
-                                           : launch_grouped_f64(np, *gp, num_sms, persistent, s);
+            cudaError_t e = dt == TSMM_F32 ? launch_grouped_f32(np, unaligned, *gp, s)
+                                           : launch_grouped_f64(np, unaligned, *gp, s);
             if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? TSMM_ERR_OUT_OF_MEMORY : TSMM_ERR_CUDA;
         }
     }
@@ -156,5 +166,5 @@ tsmm_status tsmm::execute_grouped(const tsmm_group_item *items, int count, tsmm_
 
 extern "C" tsmm_status tsmm_execute_grouped(const tsmm_group_item *items, int count,
                                             tsmm_stream_t stream) {
-    return tsmm::execute_grouped(items, count, stream, true);
+    return tsmm::execute_grouped(items, count, stream);
 }

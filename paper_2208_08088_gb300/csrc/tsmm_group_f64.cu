@@ -2,8 +2,7 @@
 #include "tsmm_group.cuh"
 
 namespace tsmm {
-cudaError_t launch_grouped_f64(int np, const GroupParams &gp, int num_sms, bool persistent,
-                               cudaStream_t s) {
-    return launch_grouped_dispatch<double>(np, gp, num_sms, persistent, s);
+cudaError_t launch_grouped_f64(int np, bool unaligned, const GroupParams &gp, cudaStream_t s) {
+    return launch_grouped_dispatch<double>(np, unaligned, gp, s);
 }
 }  // namespace tsmm

@@ -209,12 +209,8 @@ cudaError_t launch_rankk_bf16x3(const CUtensorMap *tmA, const CUtensorMap *tmC, 
 int plan_cache_lookup(tsmm_dtype dtype, int64_t m, int64_t n, int64_t k, int sms);
 void plan_cache_store(tsmm_dtype dtype, int64_t m, int64_t n, int64_t k, int sms, int splits);
 
-// tsmm_execute_grouped with a choice of grid: persistent (the exported entry
-// point: RESIDENT blocks per SM loop over the items) or one block per item (the
-// server's lower-priority work, which then yields SMs to higher-priority
-// streams as its items finish).  Results are the same either way.
-tsmm_status execute_grouped(const tsmm_group_item *items, int count, tsmm_stream_t stream,
-                            bool persistent);
+// tsmm_execute_grouped (tsmm_group_api.cu), for the server.
+tsmm_status execute_grouped(const tsmm_group_item *items, int count, tsmm_stream_t stream);
 
 // Split-K factor of the regime (i) kernel (planner model in tsmm_api.cu);
 // `resident` = thread blocks per SM.

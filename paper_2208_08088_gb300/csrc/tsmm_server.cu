@@ -15,11 +15,10 @@
 //     completion event: a small request is done when its sub-batch is, not when
 //     the largest request launched with it is.  Each lane has three
 //     high-priority streams and one low-priority stream: the first sub-batch
-//     runs as persistent launches, one per kernel class, side by side on the
-//     high-priority streams; the rest run one block per item on the
-//     low-priority one, so that the GPU's block scheduler hands SMs to newly
-//     launched small work as items finish instead of after a whole persistent
-//     launch;
+//     runs as grouped launches, one per kernel class, side by side on the
+//     high-priority streams; the rest run on the low-priority one.  A grouped
+//     launch has one block per work item, so the GPU's block scheduler hands
+//     SMs to newly launched small work as items finish;
 //   * detects sub-batch completion with CUDA events, records completion times
 //     and returns the sub-batch's memory to the budget and the arena.  Each
 //     launch unit has its own device status word, so a bounded wait that gave
@@ -219,18 +218,23 @@ void tsmm_server_s::launch(double t) {
     struct Unit {
         std::vector<Req *> reqs;
         cudaStream_t st;
-        bool persistent;
     };
     std::vector<Unit> units;
     {
         std::map<int, std::vector<Req *>> by_class;
-        for (size_t i = 0; i < cuts[0]; ++i) by_class[reqs[i]->plan.regime * 256 + reqs[i]->plan.np].push_back(reqs[i]);
+        for (size_t i = 0; i < cuts[0]; ++i) {
+            // kernel class: regime, padded width, and whether a tensor map can describe A
+            const tsmm_request &r = reqs[i]->r;
+            const int64_t es = (int64_t)dtype_size(reqs[i]->plan.dtype);
+            const bool unaligned = reinterpret_cast<uintptr_t>(r.A_dev) % 16 != 0 || (r.lda * es) % 16 != 0;
+            by_class[reqs[i]->plan.regime * 256 + (unaligned ? 128 : 0) + reqs[i]->plan.np].push_back(reqs[i]);
+        }
         int h = 0;
         for (auto &kv : by_class)
-            units.push_back(Unit{std::move(kv.second), streams[kLaneStreams * s + (h++ % kHighStreams)], true});
+            units.push_back(Unit{std::move(kv.second), streams[kLaneStreams * s + (h++ % kHighStreams)]});
         for (size_t c = 1; c < cuts.size(); ++c)
             units.push_back(Unit{std::vector<Req *>(reqs.begin() + cuts[c - 1], reqs.begin() + cuts[c]),
-                                 streams[kLaneStreams * s + kHighStreams], false});
+                                 streams[kLaneStreams * s + kHighStreams]});
     }
     tsmm_status st = TSMM_OK;
     for (Unit &u : units) {
@@ -260,7 +264,7 @@ void tsmm_server_s::launch(double t) {
                     const tsmm_request &r = q->r;
                     items[i] = tsmm_group_item{&q->plan, r.alpha, r.A_dev, r.lda, r.pb, r.beta, r.C_dev, r.ldc};
                 }
-                st = execute_grouped(items.data(), (int)items.size(), u.st, u.persistent);
+                st = execute_grouped(items.data(), (int)items.size(), u.st);
                 if (st == TSMM_OK && inject_units.load() > 0) {
                     // diagnostics: leave what a block that gave up leaves -- the unit's
                     // status word set and its arrival counters part-way

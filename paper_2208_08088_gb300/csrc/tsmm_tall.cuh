@@ -294,9 +294,12 @@ struct TallAcc<float, NP> {
                                            AccTile<float, Cfg::R, Cfg::CN, Cfg::BV>>::type;
 };
 
+// One block's work item (m-slab `slab`, k range `split`) with A described by
+// the tensor map *tmA (a kernel parameter); the body of the single-problem
+// kernel and of the grouped kernel.
 template <typename T, int NP>
-__global__ void __launch_bounds__(TallCfg<T, NP>::THREADS, TallCfg<T, NP>::RESIDENT)
-    tall_tma_kernel(const __grid_constant__ CUtensorMap tmA, const TallArgs a) {
+__device__ __forceinline__ void tall_tma_block(const CUtensorMap *tmA, const TallArgs &a, int64_t slab,
+                                               int split) {
     using Cfg = TallCfg<T, NP>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     T *sA = reinterpret_cast<T *>(smem_raw);
@@ -308,14 +311,12 @@ __global__ void __launch_bounds__(TallCfg<T, NP>::THREADS, TallCfg<T, NP>::RESID
 
     const int warp = threadIdx.x / 32;
     const int lane = threadIdx.x % 32;
-    const int64_t slab = blockIdx.x;
-    const int split = blockIdx.y;
     const int64_t k0 = (int64_t)split * a.kchunk;
     const int64_t k1 = (k0 + a.kchunk < a.kp) ? k0 + a.kchunk : a.kp;
     const int iters = (int)((k1 - k0) / Cfg::BKS);
 
     if (threadIdx.x == 0) {
-        prefetch_tmap(&tmA);
+        prefetch_tmap(tmA);
         for (int s = 0; s < Cfg::STAGES; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], Cfg::NWARPS);
@@ -341,7 +342,7 @@ __global__ void __launch_bounds__(TallCfg<T, NP>::THREADS, TallCfg<T, NP>::RESID
                 }
                 const int64_t kk = k0 + (int64_t)it * Cfg::BKS;
                 mbar_arrive_expect_tx(&full[st], Cfg::STAGE_BYTES);
-                tma_load_2d(sA + st * Cfg::A_STAGE, &tmA, (int32_t)(slab * Cfg::BM), (int32_t)kk,
+                tma_load_2d(sA + st * Cfg::A_STAGE, tmA, (int32_t)(slab * Cfg::BM), (int32_t)kk,
                             &full[st], pol_a);
                 bulk_load(sB + st * Cfg::B_STAGE, Bp + kk * NP, Cfg::B_STAGE * (int)sizeof(T),
                           &full[st], pol_b);
@@ -398,6 +399,12 @@ __global__ void __launch_bounds__(TallCfg<T, NP>::THREADS, TallCfg<T, NP>::RESID
     }
     named_barrier(1, Cfg::CONSUMERS);
     tall_finish<T, NP>(red, a, slab, split, threadIdx.x, flag);
+}
+
+template <typename T, int NP>
+__global__ void __launch_bounds__(TallCfg<T, NP>::THREADS, TallCfg<T, NP>::RESIDENT)
+    tall_tma_kernel(const __grid_constant__ CUtensorMap tmA, const TallArgs a) {
+    tall_tma_block<T, NP>(&tmA, a, blockIdx.x, (int)blockIdx.y);
 }
 
 // Same decomposition without a tensor map, for an A that one cannot describe
@@ -459,8 +466,7 @@ struct AsyncCfg {
 };
 
 template <typename T, int NP>
-__global__ void __launch_bounds__(TallCfg<T, NP>::THREADS, TallCfg<T, NP>::RESIDENT)
-    tall_async_kernel(const TallArgs a) {
+__device__ __forceinline__ void tall_async_block(const TallArgs &a, int64_t slab, int split) {
     using Cfg = TallCfg<T, NP>;
     using AC = AsyncCfg<T, NP>;
     constexpr int S = AC::STAGES;
@@ -475,8 +481,6 @@ __global__ void __launch_bounds__(TallCfg<T, NP>::THREADS, TallCfg<T, NP>::RESID
 
     const int warp = threadIdx.x / 32;
     const int lane = threadIdx.x % 32;
-    const int64_t slab = blockIdx.x;
-    const int split = blockIdx.y;
     const int64_t k0 = (int64_t)split * a.kchunk;
     const int64_t k1 = (k0 + a.kchunk < a.kp) ? k0 + a.kchunk : a.kp;
     const int iters = (int)((k1 - k0) / Cfg::BKS);
@@ -595,6 +599,12 @@ __global__ void __launch_bounds__(TallCfg<T, NP>::THREADS, TallCfg<T, NP>::RESID
     }
     named_barrier(1, Cfg::CONSUMERS);
     tall_finish<T, NP>(red, a, slab, split, threadIdx.x, flag);
+}
+
+template <typename T, int NP>
+__global__ void __launch_bounds__(TallCfg<T, NP>::THREADS, TallCfg<T, NP>::RESIDENT)
+    tall_async_kernel(const TallArgs a) {
+    tall_async_block<T, NP>(a, blockIdx.x, (int)blockIdx.y);
 }
 
 template <typename T, int NP>

@@ -65,6 +65,49 @@ def test_grouped_equals_single_launches(dtype):
         assert_parity(C, A, B, C0 if beta != 0 else None, alpha, beta)
 
 
+UNALIGNED_MIX = [  # (m, n, k, a_offset, lda_pad): A not describable by a tensor map
+    (1027, 1, 333, 0, 1), (2050, 5, 3001, 1, 0), (777, 16, 20000, 3, 2), (4099, 24, 1500, 2, 1),
+    (515, 33, 700, 1, 3), (1030, 48, 2222, 0, 2), (2047, 64, 5000, 3, 0), (129, 8, 40, 2, 1),
+]
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+def test_grouped_unaligned_mix_equals_single_launches(dtype):
+    """Problems whose A has a column stride or base that is not 16-byte aligned
+    run in the grouped kernel's element/bulk-copy form: bit for bit the single
+    launches (same plan, same arithmetic) and exact against the oracle on
+    integer inputs, over every padded width, every offset within 16 bytes,
+    split-K and ragged slabs."""
+    probs = []
+    for i, (m, n, k, off, pad) in enumerate(UNALIGNED_MIX):
+        A = ti.matrix_np(m, k, 300 + 10 * i, "integer", dtype)
+        B = ti.matrix_np(k, n, 301 + 10 * i, "integer", dtype)
+        C0 = ti.matrix_np(m, n, 302 + 10 * i, "integer", dtype)
+        dA = to_device(A, ld=m + pad, offset=off)
+        probs.append((m, n, k, A, B, C0, dA, tsmm.pack_b(to_device(B))))
+    singles = []
+    for (m, n, k, A, B, C0, dA, pb) in probs:
+        dC = to_device(C0)
+        pl = tsmm.plan(m, n, k, T[dtype])
+        tsmm.execute(pl, 1.5, dA, pb, 0.5, dC)
+        pl.check()
+        singles.append(dC.cpu().numpy())
+    plans, outs, items = [], [], []
+    for (m, n, k, A, B, C0, dA, pb) in probs:
+        pl = tsmm.plan(m, n, k, T[dtype])
+        dC = to_device(C0)
+        plans.append(pl)
+        outs.append(dC)
+        items.append((pl, 1.5, dA, pb, 0.5, dC))
+    tsmm.execute_grouped(items)
+    for pl in plans:
+        pl.check()
+    for i, (m, n, k, A, B, C0, dA, pb) in enumerate(probs):
+        C = outs[i].cpu().numpy()
+        assert np.array_equal(C, singles[i]), f"problem {i} differs from its single launch"
+        assert_parity(C, A, B, C0, 1.5, 0.5, exact=True)
+
+
 def test_grouped_many_problems_span_several_launches():
     """60 problems of one class exceed the 48-per-launch limit."""
     dtype = np.float32

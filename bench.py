@@ -6,7 +6,9 @@ the shared seeded generator, B packed once per n (packing untimed, as in the
 paper's evaluation, Section V).  One step = one tsmm_execute per (n, beta)
 point, 14 launches over a resident 4 GiB A (larger than L2, so no flush is
 needed between calls).  `--dtype f64` runs the same sweep in FP64.
-`--workload rankk` runs m = n = 16384, k in {4,...,128}, beta = 1.
+`--workload rankk` runs m = n = 16384, k in {4,...,128}, beta = 1;
+`--workload grouped` times tsmm_execute_grouped against back-to-back single
+launches on mixes of uneven problems.
 
 Metric: GFLOP/s by Eq. 7 (2*m*n*k / t) aggregated over the step, with the
 roofline of the dominant kernel against peaks measured in the same run (the
@@ -18,7 +20,7 @@ the host cores is timed on a bounded sample of the same workload as a
 baseline, with all cores and with one.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--dtype f32|f64]
-                  [--workload tall|rankk|precision|serving] [--impl ours|reference]
+                  [--workload tall|rankk|precision|serving|grouped] [--impl ours|reference]
                   [--split replicas|rows]
 
 Under torchrun (N > 1) every rank runs the full workload on its own GPU
@@ -63,7 +65,7 @@ def parse():
     p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--dtype", choices=["f32", "f64"], default="f32")
-    p.add_argument("--workload", choices=["tall", "rankk", "precision", "serving"], default="tall")
+    p.add_argument("--workload", choices=["tall", "rankk", "precision", "serving", "grouped"], default="tall")
     p.add_argument("--requests", type=int, default=10000, help="serving: number of requests")
     p.add_argument("--load", type=float, default=0.8, help="serving: arrival rate / measured capacity")
     p.add_argument("--streams", type=int, default=4, help="serving: the server's CUDA streams")
@@ -1011,10 +1013,100 @@ def run_serving(args):
     return 0
 
 
+# (n, problems, largest m) of each grouped mix
+GROUPED_MIXES = [(1, 40, 65536), (6, 40, 65536), (16, 40, 65536), (40, 40, 65536), (64, 20, 262144),
+                 (16, 40, 8192)]
+
+
+def run_grouped(args):
+    """Grouped execution against back-to-back single launches, as its own JSON
+    line.  Each mix: FP32 problems with the same n, m log-uniform in [1024,
+    largest m] (odd), k log-uniform in [64, 8192], beta = 0, drawn from a
+    seed; once with lda = m (A not describable by a tensor map) and once with lda
+    rounded up to a multiple of 4.  Both forms run on one stream; the median of
+    7 timed repetitions (CUDA events) after one untimed; every mix's inputs are
+    larger than L2."""
+    import torch
+
+    import paper_2208_08088_gb300 as tsmm
+    import tsmm_inputs as ti
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, reps=7):
+        fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        return float(np.median(ts))
+
+    rng = np.random.default_rng(2208)
+    mixes, total_fl, total_ms = [], 0.0, 0.0
+    for mi, (n, count, mmax) in enumerate(GROUPED_MIXES):
+        for aligned in (False, True):
+            items, plans, keep = [], [], []
+            fl = byts = 0.0
+            for i in range(count):
+                m = int(np.exp(rng.uniform(np.log(1024), np.log(mmax)))) | 1
+                k = int(np.exp(rng.uniform(np.log(64), np.log(8192))))
+                ld = (m + 3) // 4 * 4 if aligned else m
+                buf = torch.empty(ld * k, dtype=torch.float32, device="cuda")
+                ti.fill_torch(buf, ti.SEED_A + 1000 * mi + i, "uniform")
+                A = buf.as_strided((m, k), (1, ld))
+                B = torch.empty((n, k), dtype=torch.float32, device="cuda")
+                ti.fill_torch(B, ti.SEED_B + 1000 * mi + i, "uniform")
+                pb = tsmm.pack_b(B.t())
+                C = torch.zeros((n, m), dtype=torch.float32, device="cuda").t()
+                pl = tsmm.plan(m, n, k, torch.float32)
+                plans.append(pl)
+                keep.append(buf)
+                items.append((pl, 1.0, A, pb, 0.0, C))
+                fl += 2.0 * m * n * k
+                byts += 4.0 * (m * k + k * n + m * n)
+            t_grouped = timed(lambda: tsmm.execute_grouped(items))
+
+            def singles():
+                for it in items:
+                    tsmm.execute(*it)
+
+            t_single = timed(singles)
+            for pl in plans:
+                pl.check()
+            total_fl += fl
+            total_ms += t_grouped
+            mixes.append({"n": n, "problems": count, "m_max": mmax, "lda": "m rounded up to 4" if aligned else "m",
+                          "gflop": round(fl / 1e9, 2), "grouped_ms": round(t_grouped, 3),
+                          "single_launches_ms": round(t_single, 3),
+                          "grouped_GBs": round(byts / t_grouped / 1e6, 1),
+                          "single_launches_GBs": round(byts / t_single / 1e6, 1),
+                          "speedup": round(t_single / t_grouped, 2)})
+            del items, plans, keep
+            torch.cuda.empty_cache()
+    line = {"metric": METRIC, "value": total_fl / total_ms / 1e6, "unit": UNIT, "n_gpus": 1,
+            "steps": 7, "warmup": 1, "ms_per_step": total_ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "grouped execution vs back-to-back single launches: FP32 mixes of 20-40 "
+                                   "problems, m log-uniform [1024, m_max], k log-uniform [64, 8192], beta = 0, "
+                                   "lda = m and lda rounded up to 4; inputs larger than L2",
+                       "mixes": len(mixes)},
+            "mixes": mixes}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     args = parse()
     if args.workload == "serving" and args.impl != "reference":
         return run_serving(args)
+    if args.workload == "grouped" and args.impl != "reference":
+        return run_grouped(args)
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "precision":

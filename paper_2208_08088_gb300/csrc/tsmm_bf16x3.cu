@@ -974,6 +974,7 @@ __global__ void __launch_bounds__(512, 1)
                     if (lane == 0) mbar_arrive(&c_store[st]);
                 } else {
                     if (use_c0) {
+                        release_reads_to_async_copy();
                         __syncwarp();
                         if (lane == 0) mbar_arrive(&c_empty[st]);
                     }

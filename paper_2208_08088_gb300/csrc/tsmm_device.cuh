@@ -51,6 +51,13 @@ __device__ __forceinline__ void fence_proxy_async_smem() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
+// A consumer's release of a shared-memory buffer that a tensor or bulk copy
+// (the async proxy) refills: its reads of the buffer (generic proxy) are
+// ordered before that copy by this fence, issued by every reading thread before
+// the warp's arrival on the buffer's "empty" barrier.  Without it a read still
+// in flight when the barrier completes can return the refilled data.
+__device__ __forceinline__ void release_reads_to_async_copy() { fence_proxy_async_smem(); }
+
 __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
                  "r"(bytes)

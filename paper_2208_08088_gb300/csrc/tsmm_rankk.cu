@@ -330,6 +330,7 @@ __global__ void __launch_bounds__(RankCfg<T>::CONSUMERS + 32, 2)
             }
             RankEpilogue<T> e0;
             e0.load(a, i0, tile, tm, tn, vec_c, sC + b * Cfg::C_TILE, ebeta);
+            release_reads_to_async_copy();
             __syncwarp();
             if (lane == 0) mbar_arrive(&cempty[b]);  // C0 buffer b may be refilled
             acc.init(e0.c0v);
@@ -346,6 +347,7 @@ __global__ void __launch_bounds__(RankCfg<T>::CONSUMERS + 32, 2)
             const int kcnt = (int)((a.k - kc < Cfg::KC) ? a.k - kc : Cfg::KC);
             const T *sA = sStage + st * TC::STAGE_ELEMS;
             acc.chunk(sA, sA + Cfg::A_CHUNK, kcnt, tm, tn);
+            release_reads_to_async_copy();
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty[st]);
         }
@@ -366,6 +368,7 @@ __global__ void __launch_bounds__(RankCfg<T>::CONSUMERS + 32, 2)
         }
         ep.load(a, i0, tile, tm, tn, vec_c, want_c0 ? sC + b * Cfg::C_TILE : nullptr, ebeta);
         if (want_c0) {
+            release_reads_to_async_copy();
             __syncwarp();
             if (lane == 0) mbar_arrive(&cempty[b]);  // C0 buffer b may be refilled
         }
@@ -675,6 +678,7 @@ __global__ void __launch_bounds__(WideCfg<TMA_EPI, KC>::THREADS, WideCfg<TMA_EPI
             const int kcnt = (int)((a.k - kc < W::KC) ? a.k - kc : W::KC);
             const float *sA = sStage + st * W::STAGE_ELEMS;
             acc.chunk<W::KC>(sA, sA + W::A_CHUNK, kcnt, r0, c0);
+            release_reads_to_async_copy();
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty[st]);
         }

@@ -377,6 +377,7 @@ __device__ __forceinline__ void tall_tma_block(const CUtensorMap *tmA, const Tal
             const Vec<T, Cfg::R> av = tall_load_rows<Cfg, T>(As + col * Cfg::BM, rloc);
             acc.fma_column(av, Bs + col * NP + cloc);
         }
+        release_reads_to_async_copy();
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[st]);
     }
@@ -462,6 +463,7 @@ struct AsyncCfg {
         STAGES * STAGE_BYTES > RED_BYTES ? STAGES * STAGE_BYTES : RED_BYTES;
     static constexpr int SMEM = DATA_BYTES + 2 * STAGES * 8 + 16;
     static_assert(Cfg::BKS == 32, "one producer lane per column");
+    static_assert(Cfg::KPW % V == 0, "a warp's first stage column is a multiple of V");
     static_assert(Cfg::RESIDENT * (SMEM + 1024) <= 228 * 1024, "resident blocks per SM");
 };
 
@@ -559,6 +561,11 @@ __device__ __forceinline__ void tall_async_block(const TallArgs &a, int64_t slab
     const int cloc = g * Cfg::CN;
     typename TallAcc<T, NP>::type acc;
     acc.zero();
+    // every stage starts at a multiple of BKS (k splits are whole stages), so a
+    // column's offset within 16 bytes depends only on its index mod V
+    int doff[V];
+#pragma unroll
+    for (int j = 0; j < V; ++j) doff[j] = col_off(k0 + j);
 
     bool ok = true;
     for (int it = 0; it < iters; ++it) {
@@ -569,16 +576,16 @@ __device__ __forceinline__ void tall_async_block(const TallArgs &a, int64_t slab
         }
         const T *As = sA + st * AC::A_STAGE;
         const T *Bs = sB + st * Cfg::B_STAGE;
-        const int64_t kk = k0 + (int64_t)it * Cfg::BKS;
 #pragma unroll
         for (int c = 0; c < Cfg::KPW; ++c) {
             const int col = wk * Cfg::KPW + c;
-            const T *colp = As + col * AC::APAD + col_off(kk + col);
+            const T *colp = As + col * AC::APAD + doff[c % V];  // col = c mod V: KPW % V == 0
             Vec<T, Cfg::R> av;
 #pragma unroll
             for (int r = 0; r < Cfg::R; ++r) av.v[r] = colp[Cfg::row(rloc, r)];
             acc.fma_column(av, Bs + col * NP + cloc);
         }
+        release_reads_to_async_copy();
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[st]);
     }

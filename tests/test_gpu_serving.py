@@ -72,13 +72,49 @@ def test_serving_same_alone_and_in_mix():
     mix, comps = run(srv, bs, reqs, spread_s=0.02, seed=2)
     srv.close()
     for q in reqs:
-        assert np.array_equal(mix[q["id"]], alone[q["id"]]), f"request {q['id']} differs"
         k, n, B, pb = bs[q["b"]]
         Cref, E = oracle.tsmm(q["alpha"], q["A"], B, q["beta"], q["C0"] if q["beta"] else None)
+        if not np.array_equal(mix[q["id"]], alone[q["id"]]):
+            where = np.argwhere(mix[q["id"]] != alone[q["id"]])
+            verdict = {tag: oracle.check(r, Cref, E, np.float32)[2] for tag, r in
+                       (("alone", alone[q["id"]]), ("mix", mix[q["id"]]))}
+            raise AssertionError(f"request {q['id']} (m={q['m']}, k={k}, n={n}, beta={q['beta']}) differs "
+                                 f"in {len(where)} entries, first {where[:4].tolist()}; entries outside "
+                                 f"the oracle's bound: {verdict}")
         ok, ratio, nbad = oracle.check(mix[q["id"]], Cref, E, np.float32)
         assert ok, f"request {q['id']}: {nbad} entries outside the bound"
     for c in comps.values():
         assert c["arrival_s"] <= c["admit_s"] <= c["launch_s"] <= c["complete_s"]
+
+
+def test_serving_mix_repeats_bitwise_under_concurrency():
+    """Eight mixes of the same 40 requests, each with its own arrival order,
+    against one direct tsmm_execute per request: every result identical bit
+    for bit.  Grouped launches of several kernel classes then run side by side
+    on the server's streams, which is what exposed a consumer's shared-memory
+    reads of a ring stage racing the copy that refills it (the release fence
+    before each empty-barrier arrival); without that fence about one mix in
+    four had one k term of one warp wrong."""
+    bs = make_bs()
+    reqs = make_requests(bs, 40, seed=1)
+    direct = {}
+    for q in reqs:
+        k, n, B, pb = bs[q["b"]]
+        dA, dC = to_device(q["A"]), to_device(q["C0"])
+        pl = tsmm.plan(q["m"], n, k, torch.float32)
+        tsmm.execute(pl, q["alpha"], dA, pb, q["beta"], dC)
+        pl.check()
+        direct[q["id"]] = dC.cpu().numpy()
+    for trial in range(8):
+        srv = tsmm.Server(budget_bytes=8 << 30, num_streams=4, max_batch=16)
+        mix, _ = run(srv, bs, reqs, spread_s=0.02, seed=100 + trial)
+        srv.close()
+        for q in reqs:
+            i = q["id"]
+            if not np.array_equal(mix[i], direct[i]):
+                rows = np.unique(np.argwhere(mix[i] != direct[i])[:, 0])
+                raise AssertionError(f"mix {trial}: request {i} differs from its direct launch in rows "
+                                     f"{rows[0]}..{rows[-1]} ({len(rows)} rows)")
 
 
 def test_serving_admission_respects_budget_and_batches_overlap():

@@ -871,6 +871,28 @@ def run_precision(args):
     return 0
 
 
+def longest_stall_ms(comps):
+    """Longest interval with a request outstanding (arrived, not complete)
+    and no completion: a pause of the server or the GPU, not queueing.
+    Between consecutive completions a < b, the requests completing at b
+    or later that arrived before b are outstanding from their arrival on;
+    the earliest of those arrivals (a suffix minimum in completion order)
+    starts the interval, clipped at a."""
+    order = sorted(comps, key=lambda c: c["complete_s"])
+    done = np.array([c["complete_s"] for c in order])
+    arr = np.array([c["arrival_s"] for c in order])
+    first = np.minimum.accumulate(arr[::-1])[::-1]  # earliest arrival among completions i..end
+    best = 0.0
+    for i in range(1, len(order)):
+        if first[i] < done[i]:
+            best = max(best, done[i] - max(done[i - 1], first[i]))
+    return round(float(best) * 1e3, 2)
+
+
+# arrival rates of the serving load sweep, as fractions of the measured capacity
+SERVING_LOADS = (0.5, 0.7, 0.9, 0.95)
+
+
 def serving_session(args, tsmm, torch, N, load, num_streams):
     """Serving workload: 32 device-resident packed B (k log-uniform in
     [64, 8192], n log-uniform in [1, 64], drawn once from a seed); requests pick a
@@ -879,7 +901,9 @@ def serving_session(args, tsmm, torch, N, load, num_streams):
     under a 40 GB budget and batches continuously (grouped launches, one block per work item, on
     `num_streams` lanes).  Capacity is measured with every request arriving at
     once; then Poisson arrivals at `load` x capacity give the p50 / p90 / p99
-    arrival-to-completion latency and the aggregate GFLOP/s.
+    arrival-to-completion latency and the aggregate GFLOP/s, and the same
+    arrival sequence rescaled to each rate of SERVING_LOADS gives the latency
+    sweep (`load_sweep`).
 
     A requests read windows of one resident, read-only pool (moving 10,000 A
     matrices over the host link would measure the link); the budget charges each
@@ -960,16 +984,31 @@ def serving_session(args, tsmm, torch, N, load, num_streams):
     makespan = max(c["complete_s"] for c in comps) - t0
     capacity = N / makespan
     cap_gflops = fl.sum() / makespan / 1e9
-    # open loop: Poisson arrivals at load x capacity
+    # open loop: Poisson arrivals at load x capacity (one seeded draw of unit
+    # gaps, scaled to each rate), then the same at each load of the sweep
+    unit_gaps = rng.exponential(1.0, N)
+
+    def open_loop(ld):
+        t0 = tsmm.tsmm_server_clock() + 0.05
+        comps = session(t0 + np.cumsum(unit_gaps / (ld * capacity)))
+        lat = np.array([c["complete_s"] - c["arrival_s"] for c in comps])
+        span = max(c["complete_s"] for c in comps) - min(c["arrival_s"] for c in comps)
+        return comps, lat, span
+
     lam = load * capacity
-    gaps = rng.exponential(1.0 / lam, N)
-    t0 = tsmm.tsmm_server_clock() + 0.05
-    arrivals = t0 + np.cumsum(gaps)
-    comps = session(arrivals)
-    lat = np.array([c["complete_s"] - c["arrival_s"] for c in comps])
+    comps, lat, span = open_loop(load)
     qwait = np.array([c["admit_s"] - c["arrival_s"] for c in comps])
     lwait = np.array([c["launch_s"] - c["arrival_s"] for c in comps])
-    span = max(c["complete_s"] for c in comps) - min(c["arrival_s"] for c in comps)
+    stall_main = longest_stall_ms(comps)
+    sweep = []
+    for ld in SERVING_LOADS:
+        cs, lt, sp = open_loop(ld)
+        sweep.append({"load": ld, "arrival_rate_per_s": round(ld * capacity, 1),
+                      "gflops": round(fl.sum() / sp / 1e9, 1),
+                      "p50_ms": round(float(np.percentile(lt, 50)) * 1e3, 3),
+                      "p90_ms": round(float(np.percentile(lt, 90)) * 1e3, 3),
+                      "p99_ms": round(float(np.percentile(lt, 99)) * 1e3, 3),
+                      "longest_stall_ms": longest_stall_ms(cs)})
     srv.close()
     del a_pool, c_pool, packed
     torch.cuda.empty_cache()
@@ -985,10 +1024,12 @@ def serving_session(args, tsmm, torch, N, load, num_streams):
                            "mean": round(float(lat.mean()) * 1e3, 3),
                            "queue_wait_p99": round(float(np.percentile(qwait, 99)) * 1e3, 3),
                            "launch_wait_p50": round(float(np.percentile(lwait, 50)) * 1e3, 3),
-                           "launch_wait_p99": round(float(np.percentile(lwait, 99)) * 1e3, 3)},
+                           "launch_wait_p99": round(float(np.percentile(lwait, 99)) * 1e3, 3),
+                           "longest_stall_ms": stall_main},
             "capacity": {"requests_per_s": round(capacity, 1), "gflops": round(cap_gflops, 1),
                          "makespan_ms": round(makespan * 1e3, 2)},
             "arrival_rate_per_s": round(lam, 1),
+            "load_sweep": sweep,
             "plans": f"autotuned: {len(seen)} shapes (one per packed B and quarter octave of m), "
                      f"{tune_s:.1f} s, before the sessions",
             "a_storage": "windows of one read-only resident pool, each charged in full to the budget"}
@@ -1008,7 +1049,7 @@ def run_serving(args):
             "config": {"workload": "serving: " + r["workload"], "total_gflop": r["total_gflop"],
                        "plans": r["plans"], "a_storage": r["a_storage"]},
             "latency_ms": r["latency_ms"], "capacity": r["capacity"],
-            "arrival_rate_per_s": r["arrival_rate_per_s"]}
+            "arrival_rate_per_s": r["arrival_rate_per_s"], "load_sweep": r["load_sweep"]}
     print(json.dumps(line))
     return 0
 

@@ -58,3 +58,24 @@ def test_workloads_and_roofline_arithmetic():
     assert bench.alg_bytes(10, 2, 3, 0.5, 8) == 8 * (30 + 6 + 40)
     # the derived FP32 peak: 152 SMs x 128 lanes x 2 flop x 2070 MHz
     assert abs(bench.SMS * bench.FP32_LANES_PER_SM * 2 * bench.SM_MAX_MHZ * 1e6 / 1e12 - 80.55) < 0.01
+
+
+def test_serving_stall_metric():
+    """longest_stall_ms: the longest interval with a request outstanding and no
+    completion.  A 100-ms pause that holds the requests arriving in it shows as
+    the pause; an idle gap with nothing outstanding does not count; a request
+    outstanding from time 0 counts from its arrival."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    comps = []
+    for i in range(100):
+        a = i * 0.001
+        c = 0.15 + 0.0001 * i if 0.05 <= a < 0.15 else a + 0.0005
+        comps.append({"arrival_s": a, "complete_s": c})
+    assert abs(bench.longest_stall_ms(comps) - 105.0) < 1e-6
+    idle = [{"arrival_s": 0.0, "complete_s": 0.001}, {"arrival_s": 0.5, "complete_s": 0.501}]
+    assert abs(bench.longest_stall_ms(idle) - 1.0) < 1e-6
+    held = [{"arrival_s": 0.0, "complete_s": 0.001}, {"arrival_s": 0.0, "complete_s": 0.2}]
+    assert abs(bench.longest_stall_ms(held) - 199.0) < 1e-6
+    assert bench.longest_stall_ms(held[:1]) == 0.0

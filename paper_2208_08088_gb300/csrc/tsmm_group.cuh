@@ -13,7 +13,9 @@
 // workspace; the results are the single launches' bit for bit.
 //
 // U = true: problems whose A a tensor map cannot describe (base or column
-// stride not a multiple of 16 bytes) run the bulk/element-copy block body.
+// stride not a multiple of 16 bytes) run the bulk/element-copy block body, in
+// its load form LV (async_load_variant: the same for every problem of the
+// launch).
 #pragma once
 #include <climits>
 #include "tsmm_tall.cuh"
@@ -41,7 +43,7 @@ __device__ __forceinline__ int group_find(const GroupParams &gp, int64_t item) {
     return p;
 }
 
-template <typename T, int NP, bool U>
+template <typename T, int NP, bool U, int LV>
 __global__ void __launch_bounds__(TallCfg<T, NP>::THREADS, TallCfg<T, NP>::RESIDENT)
     tall_grouped_kernel(const __grid_constant__ GroupParams gp) {
     const int64_t item = blockIdx.x;
@@ -50,45 +52,49 @@ __global__ void __launch_bounds__(TallCfg<T, NP>::THREADS, TallCfg<T, NP>::RESID
     int64_t slab, split;
     udivmod(item - gp.p[p].item_begin, a.splits, slab, split);
     if constexpr (U)
-        tall_async_block<T, NP>(a, slab, (int)split);
+        tall_async_block<T, NP, LV>(a, slab, (int)split);
     else
         tall_tma_block<T, NP>(&gp.p[p].tmA, a, slab, (int)split);
 }
 
-template <typename T, int NP, bool U>
+template <typename T, int NP, bool U, int LV>
 cudaError_t launch_grouped_t(const GroupParams &gp, cudaStream_t s) {
     const int smem = U ? AsyncCfg<T, NP>::SMEM : TallCfg<T, NP>::SMEM;
     {
         const cudaError_t e =
-            ensure_smem_limit(reinterpret_cast<const void *>(tall_grouped_kernel<T, NP, U>), smem);
+            ensure_smem_limit(reinterpret_cast<const void *>(tall_grouped_kernel<T, NP, U, LV>), smem);
         if (e != cudaSuccess) return e;
     }
     if (gp.total_items <= 0) return cudaSuccess;
     if (gp.total_items > INT_MAX) return cudaErrorInvalidValue;
-    tall_grouped_kernel<T, NP, U><<<(unsigned)gp.total_items, TallCfg<T, NP>::THREADS, smem, s>>>(gp);
+    tall_grouped_kernel<T, NP, U, LV><<<(unsigned)gp.total_items, TallCfg<T, NP>::THREADS, smem, s>>>(gp);
     return cudaGetLastError();
 }
 
-// unaligned: problems whose A a tensor map cannot describe (the U kernel)
+template <typename T, int NP>
+cudaError_t launch_grouped_np(bool unaligned, int lv, const GroupParams &gp, cudaStream_t s) {
+    if (!unaligned) return launch_grouped_t<T, NP, false, -1>(gp, s);
+    return with_load_variant<T, NP>(lv, [&](auto lv_tag) {
+        return launch_grouped_t<T, NP, true, decltype(lv_tag)::value>(gp, s);
+    });
+}
+
+// unaligned: problems whose A a tensor map cannot describe (the U kernel, in
+// load form lv)
 template <typename T>
-cudaError_t launch_grouped_dispatch(int np, bool unaligned, const GroupParams &gp, cudaStream_t s) {
-#define TSMM_GROUP_CASE(NPV)                                                    \
-    case NPV:                                                                   \
-        return unaligned ? launch_grouped_t<T, NPV, true>(gp, s) : launch_grouped_t<T, NPV, false>(gp, s);
+cudaError_t launch_grouped_dispatch(int np, bool unaligned, int lv, const GroupParams &gp, cudaStream_t s) {
     switch (np) {
-        TSMM_GROUP_CASE(1)
-        TSMM_GROUP_CASE(2)
-        TSMM_GROUP_CASE(4)
-        TSMM_GROUP_CASE(8)
-        TSMM_GROUP_CASE(16)
-        TSMM_GROUP_CASE(24)
-        TSMM_GROUP_CASE(32)
-        TSMM_GROUP_CASE(48)
-        TSMM_GROUP_CASE(64)
-        default:
-            return cudaErrorInvalidValue;
+        case 1: return launch_grouped_np<T, 1>(unaligned, lv, gp, s);
+        case 2: return launch_grouped_np<T, 2>(unaligned, lv, gp, s);
+        case 4: return launch_grouped_np<T, 4>(unaligned, lv, gp, s);
+        case 8: return launch_grouped_np<T, 8>(unaligned, lv, gp, s);
+        case 16: return launch_grouped_np<T, 16>(unaligned, lv, gp, s);
+        case 24: return launch_grouped_np<T, 24>(unaligned, lv, gp, s);
+        case 32: return launch_grouped_np<T, 32>(unaligned, lv, gp, s);
+        case 48: return launch_grouped_np<T, 48>(unaligned, lv, gp, s);
+        case 64: return launch_grouped_np<T, 64>(unaligned, lv, gp, s);
+        default: return cudaErrorInvalidValue;
     }
-#undef TSMM_GROUP_CASE
 }
 
 }  // namespace tsmm

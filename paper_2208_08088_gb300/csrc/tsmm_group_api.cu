@@ -1,7 +1,8 @@
 // tsmm_execute_grouped: many pre-packed TSMMs in as few launches as possible.
 // Regime (i) problems are batched, per dtype, padded column count and kind of
 // A (one a tensor map can describe, or one whose base or column stride is not
-// a multiple of 16 bytes), into launches of the grouped kernel (up to
+// a multiple of 16 bytes, and then its load form), into launches of the
+// grouped kernel (up to
 // kGroupMax problems and INT_MAX work items each, one block per item); every
 // other problem (regime (ii), alpha = 0, k = 0, the BF16x3 mode) is executed by
 // its own tsmm_execute launch on the same stream.
@@ -19,8 +20,8 @@
 #include "tsmm_group.cuh"
 
 namespace tsmm {
-cudaError_t launch_grouped_f32(int np, bool unaligned, const GroupParams &gp, cudaStream_t s);
-cudaError_t launch_grouped_f64(int np, bool unaligned, const GroupParams &gp, cudaStream_t s);
+cudaError_t launch_grouped_f32(int np, bool unaligned, int lv, const GroupParams &gp, cudaStream_t s);
+cudaError_t launch_grouped_f64(int np, bool unaligned, int lv, const GroupParams &gp, cudaStream_t s);
 }  // namespace tsmm
 
 using namespace tsmm;
@@ -90,12 +91,15 @@ tsmm_status tsmm::execute_grouped(const tsmm_group_item *items, int count, tsmm_
         if (!seen.insert(items[i].plan).second) return TSMM_ERR_INVALID_ARG;  // shared workspace
     }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    // classes of groupable problems: (dtype, np, kind of A) -> item indices
-    std::map<std::tuple<int, int, int>, std::vector<int>> classes;
+    // classes of groupable problems: (dtype, np, kind of A, load form) -> item indices
+    std::map<std::tuple<int, int, int, int>, std::vector<int>> classes;
     for (int i = 0; i < count; ++i) {
         const int kind = group_kind(items[i]);
         if (kind != 0) {
-            classes[std::make_tuple((int)items[i].plan->dtype, items[i].plan->np, kind)].push_back(i);
+            const tsmm_plan_t p = items[i].plan;
+            const int lv = kind == 2 ? async_load_variant(p->dtype == TSMM_F32, p->np, items[i].A_dev, items[i].lda)
+                                     : -1;
+            classes[std::make_tuple((int)p->dtype, p->np, kind, lv)].push_back(i);
         } else {
             tsmm_status st = tsmm_execute(items[i].plan, items[i].alpha, items[i].A_dev, items[i].lda,
                                           items[i].pb, items[i].beta, items[i].C_dev, items[i].ldc,
@@ -109,6 +113,7 @@ tsmm_status tsmm::execute_grouped(const tsmm_group_item *items, int count, tsmm_
         const tsmm_dtype dt = (tsmm_dtype)std::get<0>(cls.first);
         const int np = std::get<1>(cls.first);
         const bool unaligned = std::get<2>(cls.first) == 2;
+        const int lv = std::get<3>(cls.first);
         const std::vector<int> &idx = cls.second;
         // launches of at most kGroupMax problems and INT_MAX work items
         size_t q = 0;
@@ -156,8 +161,8 @@ tsmm_status tsmm::execute_grouped(const tsmm_group_item *items, int count, tsmm_
                 total += n_items;
             }
             gp->total_items = total;
-            cudaError_t e = dt == TSMM_F32 ? launch_grouped_f32(np, unaligned, *gp, s)
-                                           : launch_grouped_f64(np, unaligned, *gp, s);
+            cudaError_t e = dt == TSMM_F32 ? launch_grouped_f32(np, unaligned, lv, *gp, s)
+                                           : launch_grouped_f64(np, unaligned, lv, *gp, s);
             if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? TSMM_ERR_OUT_OF_MEMORY : TSMM_ERR_CUDA;
         }
     }

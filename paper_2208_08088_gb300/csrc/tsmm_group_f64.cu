@@ -2,7 +2,7 @@
 #include "tsmm_group.cuh"
 
 namespace tsmm {
-cudaError_t launch_grouped_f64(int np, bool unaligned, const GroupParams &gp, cudaStream_t s) {
-    return launch_grouped_dispatch<double>(np, unaligned, gp, s);
+cudaError_t launch_grouped_f64(int np, bool unaligned, int lv, const GroupParams &gp, cudaStream_t s) {
+    return launch_grouped_dispatch<double>(np, unaligned, lv, gp, s);
 }
 }  // namespace tsmm

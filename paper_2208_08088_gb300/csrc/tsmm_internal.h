@@ -58,6 +58,16 @@ inline int tall_bm(tsmm_dtype d, int np) { return tall_block_rows(d == TSMM_F64,
 // tiles fit 136 registers), else 2 (the width 48's 8 x 12 tiles need ~160).
 constexpr int tall_resident_blocks(bool f64, int np) { return (!f64 && (np == 32 || np == 64)) ? 3 : 2; }
 
+// Load form of the regime (i) kernel for an A that a tensor map cannot describe
+// (its bulk/element-copy kernel): for FP32 widths of 16 and more with A's base
+// 16-byte aligned, lda mod 4 -- every column's offset within 16 bytes is then
+// fixed by its index mod 4, and the kernel is compiled for it -- else -1
+// (offsets computed at run time).
+inline int async_load_variant(bool f32, int np, const void *A, int64_t lda) {
+    if (!f32 || np < 16 || reinterpret_cast<uintptr_t>(A) % 16 != 0) return -1;
+    return (int)((uint64_t)lda & 3u);
+}
+
 // Regime of a (k, n) pair: 1 = tall (n <= 64), 2 = rank-k (k <= 128), 0 = unsupported.
 inline int regime_of(int64_t k, int64_t n) {
     if (n <= kTallMaxN) return 1;

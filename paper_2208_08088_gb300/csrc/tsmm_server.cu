@@ -223,11 +223,14 @@ void tsmm_server_s::launch(double t) {
     {
         std::map<int, std::vector<Req *>> by_class;
         for (size_t i = 0; i < cuts[0]; ++i) {
-            // kernel class: regime, padded width, and whether a tensor map can describe A
+            // kernel class: regime, padded width, whether a tensor map can describe
+            // A, and if not the load form of the kernel that reads it
             const tsmm_request &r = reqs[i]->r;
-            const int64_t es = (int64_t)dtype_size(reqs[i]->plan.dtype);
+            const tsmm_plan_s &pl = reqs[i]->plan;
+            const int64_t es = (int64_t)dtype_size(pl.dtype);
             const bool unaligned = reinterpret_cast<uintptr_t>(r.A_dev) % 16 != 0 || (r.lda * es) % 16 != 0;
-            by_class[reqs[i]->plan.regime * 256 + (unaligned ? 128 : 0) + reqs[i]->plan.np].push_back(reqs[i]);
+            const int form = unaligned ? 1 + (1 + async_load_variant(pl.dtype == TSMM_F32, pl.np, r.A_dev, r.lda)) : 0;
+            by_class[pl.regime * 1024 + form * 128 + pl.np].push_back(reqs[i]);
         }
         int h = 0;
         for (auto &kv : by_class)

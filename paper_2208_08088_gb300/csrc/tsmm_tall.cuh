@@ -467,7 +467,52 @@ struct AsyncCfg {
     static_assert(Cfg::RESIDENT * (SMEM + 1024) <= 228 * 1024, "resident blocks per SM");
 };
 
-template <typename T, int NP>
+// f(std::integral_constant<int, I>{}) for I = B .. E-1, unrolled at compile time.
+template <int B, int E, typename F>
+__device__ __forceinline__ void static_for(F &&f) {
+    if constexpr (B < E) {
+        f(std::integral_constant<int, B>{});
+        static_for<B + 1, E>(f);
+    }
+}
+
+// An FP32 thread's rows of one stage column whose rows start D elements past
+// the 16-byte-aligned slot start.  rloc and the group stride are multiples of
+// 4, so every group of 4 rows sits D elements past a 16-byte boundary and takes
+// one 16-byte load (D = 0), two 8-byte loads (D = 2) or 4 + 8 + 4 bytes (D
+// odd): the same shared-memory wavefronts as element loads, in a quarter to
+// three quarters of the instructions.
+template <typename Cfg, int D>
+__device__ __forceinline__ Vec<float, Cfg::R> load_rows_at(const float *slot, int rloc) {
+    static_assert(Cfg::RV == 4, "groups of 4 rows");
+    Vec<float, Cfg::R> v;
+#pragma unroll
+    for (int gi = 0; gi < Cfg::RG; ++gi) {
+        const float *p = slot + D + rloc + gi * Cfg::GSTRIDE;
+        float x[4];
+        if constexpr (D == 0) {
+            const float4 q = *reinterpret_cast<const float4 *>(p);
+            x[0] = q.x, x[1] = q.y, x[2] = q.z, x[3] = q.w;
+        } else if constexpr (D == 2) {
+            const float2 q0 = *reinterpret_cast<const float2 *>(p);
+            const float2 q1 = *reinterpret_cast<const float2 *>(p + 2);
+            x[0] = q0.x, x[1] = q0.y, x[2] = q1.x, x[3] = q1.y;
+        } else {
+            const float2 q = *reinterpret_cast<const float2 *>(p + 1);  // 8-byte aligned for D = 1, 3
+            x[0] = p[0], x[1] = q.x, x[2] = q.y, x[3] = p[3];
+        }
+#pragma unroll
+        for (int r = 0; r < 4; ++r) v.v[gi * 4 + r] = x[r];
+    }
+    return v;
+}
+
+// LV >= 0 (FP32 widths of 16 and more, chosen on the host by
+// async_load_variant): A's base is 16-byte aligned and lda = LV mod 4, so
+// column c of a stage sits (c * LV) mod 4 elements into its slot, known at
+// compile time, and its rows are read with load_rows_at.  LV = -1: any A, the
+// offsets computed at run time and the rows read element by element.
+template <typename T, int NP, int LV = -1>
 __device__ __forceinline__ void tall_async_block(const TallArgs &a, int64_t slab, int split) {
     using Cfg = TallCfg<T, NP>;
     using AC = AsyncCfg<T, NP>;
@@ -567,6 +612,7 @@ __device__ __forceinline__ void tall_async_block(const TallArgs &a, int64_t slab
 #pragma unroll
     for (int j = 0; j < V; ++j) doff[j] = col_off(k0 + j);
 
+    static_assert(LV < 0 || (sizeof(T) == 4 && NP >= 16), "compile-time offsets: FP32 widths of 16 and more");
     bool ok = true;
     for (int it = 0; it < iters; ++it) {
         const int st = it % S;
@@ -576,15 +622,19 @@ __device__ __forceinline__ void tall_async_block(const TallArgs &a, int64_t slab
         }
         const T *As = sA + st * AC::A_STAGE;
         const T *Bs = sB + st * Cfg::B_STAGE;
-#pragma unroll
-        for (int c = 0; c < Cfg::KPW; ++c) {
-            const int col = wk * Cfg::KPW + c;
-            const T *colp = As + col * AC::APAD + doff[c % V];  // col = c mod V: KPW % V == 0
+        static_for<0, Cfg::KPW>([&](auto c_tag) {
+            constexpr int c = decltype(c_tag)::value;
+            const int col = wk * Cfg::KPW + c;  // col = c mod V: KPW % V == 0
             Vec<T, Cfg::R> av;
+            if constexpr (LV >= 0) {
+                av = load_rows_at<Cfg, (c * LV) % V>(As + col * AC::APAD, rloc);
+            } else {
+                const T *colp = As + col * AC::APAD + doff[c % V];
 #pragma unroll
-            for (int r = 0; r < Cfg::R; ++r) av.v[r] = colp[Cfg::row(rloc, r)];
+                for (int r = 0; r < Cfg::R; ++r) av.v[r] = colp[Cfg::row(rloc, r)];
+            }
             acc.fma_column(av, Bs + col * NP + cloc);
-        }
+        });
         release_reads_to_async_copy();
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[st]);
@@ -608,10 +658,10 @@ __device__ __forceinline__ void tall_async_block(const TallArgs &a, int64_t slab
     tall_finish<T, NP>(red, a, slab, split, threadIdx.x, flag);
 }
 
-template <typename T, int NP>
+template <typename T, int NP, int LV>
 __global__ void __launch_bounds__(TallCfg<T, NP>::THREADS, TallCfg<T, NP>::RESIDENT)
     tall_async_kernel(const TallArgs a) {
-    tall_async_block<T, NP>(a, blockIdx.x, (int)blockIdx.y);
+    tall_async_block<T, NP, LV>(a, blockIdx.x, (int)blockIdx.y);
 }
 
 template <typename T, int NP>
@@ -627,18 +677,46 @@ cudaError_t launch_tall_tma_t(const CUtensorMap *tmap, const TallArgs &a, cudaSt
     return cudaGetLastError();
 }
 
-template <typename T, int NP>
-cudaError_t launch_tall_async_t(const TallArgs &a, cudaStream_t s) {
-    using Cfg = TallCfg<T, NP>;
+template <typename T, int NP, int LV>
+cudaError_t launch_tall_async_lv(const TallArgs &a, cudaStream_t s) {
     const int smem = AsyncCfg<T, NP>::SMEM;
     {
         const cudaError_t e =
-            ensure_smem_limit(reinterpret_cast<const void *>(tall_async_kernel<T, NP>), smem);
+            ensure_smem_limit(reinterpret_cast<const void *>(tall_async_kernel<T, NP, LV>), smem);
         if (e != cudaSuccess) return e;
     }
     dim3 grid((unsigned)a.slabs, (unsigned)a.splits);
-    tall_async_kernel<T, NP><<<grid, Cfg::THREADS, smem, s>>>(a);
+    tall_async_kernel<T, NP, LV><<<grid, TallCfg<T, NP>::THREADS, smem, s>>>(a);
     return cudaGetLastError();
+}
+
+// Calls f(std::integral_constant<int, LV>) for the load form lv of
+// async_load_variant (only -1 where no other form is instantiated).
+template <typename T, int NP, typename F>
+auto with_load_variant(int lv, F &&f) {
+    if constexpr (sizeof(T) == 4 && NP >= 16) {
+        switch (lv) {
+            case 0:
+                return f(std::integral_constant<int, 0>{});
+            case 1:
+                return f(std::integral_constant<int, 1>{});
+            case 2:
+                return f(std::integral_constant<int, 2>{});
+            case 3:
+                return f(std::integral_constant<int, 3>{});
+            default:
+                break;
+        }
+    }
+    return f(std::integral_constant<int, -1>{});
+}
+
+template <typename T, int NP>
+cudaError_t launch_tall_async_t(const TallArgs &a, cudaStream_t s) {
+    const int lv = async_load_variant(sizeof(T) == 4, NP, a.A, a.lda);
+    return with_load_variant<T, NP>(lv, [&](auto lv_tag) {
+        return launch_tall_async_lv<T, NP, decltype(lv_tag)::value>(a, s);
+    });
 }
 
 template <typename T>

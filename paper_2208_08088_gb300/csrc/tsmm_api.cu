@@ -469,8 +469,8 @@ tsmm_status tsmm_execute(tsmm_plan_t p, double alpha, const void *A_dev, int64_t
         p->tmap_lda = lda;
     }
     if (p->precision == TSMM_PREC_BF16X3) {
-        if (!tma) return TSMM_ERR_MISALIGNED;  // this mode streams A with TMA only
         if (p->regime == 2) {
+            if (!tma) return TSMM_ERR_MISALIGNED;  // regime (ii) in this mode streams A with TMA only
             RankArgs ra;
             ra.m = m;
             ra.n = n;
@@ -492,7 +492,8 @@ tsmm_status tsmm_execute(tsmm_plan_t p, double alpha, const void *A_dev, int64_t
             }
             return cuda_status(launch_rankk_bf16x3(&p->tmap, tmc ? &p->tmapc : nullptr, ra, p->status, s));
         }
-        return cuda_status(launch_tall_bf16x3(p->np, &p->tmap, a, p->num_sms, s));
+        // regime (i): an A that a tensor map cannot describe is moved column by column
+        return cuda_status(launch_tall_bf16x3(p->np, tma ? &p->tmap : nullptr, a, p->num_sms, s));
     }
     if (p->regime == 2) {
         RankArgs ra;

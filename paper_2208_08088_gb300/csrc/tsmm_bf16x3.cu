@@ -97,9 +97,14 @@ __device__ __forceinline__ int kmaj_off(int row, int k) {
     return (row >> 3) * kSBO + (k >> 3) * kLBO + (row & 7) * 16 + (k & 7) * 2;
 }
 
-template <int NP>
+// U: an A that a tensor map cannot describe; each FP32 column of a stage then
+// sits in a slot of A_STRIDE rows, at its own offset within 16 bytes.
+template <int NP, bool U = false>
 struct X3Cfg {
-    static constexpr int A_BYTES = kBM * kKB * 4;          // 32 KB: FP32 in, then BF16 hi | lo
+    static constexpr int A_STRIDE = U ? kBM + 8 : kBM;     // FP32 elements per column slot
+    static constexpr int A_FP32_BYTES = kKB * A_STRIDE * 4;
+    // FP32 in, then BF16 hi | lo (32 KB) over its start; whole KB for the MMA operands
+    static constexpr int A_BYTES = (A_FP32_BYTES + 1023) / 1024 * 1024;
     static constexpr int B_BYTES = 2 * NP * kKB * 2;       // hi + lo chunk
     static constexpr int OFF_B = kS * A_BYTES;
     static constexpr int OFF_BAR = OFF_B + kS * B_BYTES;
@@ -107,6 +112,7 @@ struct X3Cfg {
     static constexpr int SMEM = OFF_BAR + NBAR * 8 + 32;
     static constexpr int TMEM_COLS = 2 * NP < 32 ? 32 : 2 * NP;  // double-buffered accumulator
     static constexpr int THREADS = 320;
+    static_assert(SMEM <= 227 * 1024, "shared memory");
 };
 
 }  // namespace
@@ -144,10 +150,10 @@ __global__ void pack_b_bf16x3_kernel(const float *__restrict__ B, int64_t k, int
 // buffered in tensor memory (2 x NP columns) and read out by four dedicated
 // epilogue warps, so the MMAs of the next item run while the previous item's
 // results are stored; the producer and converter rings run across items.
-template <int NP>
+template <int NP, bool U>
 __global__ void __launch_bounds__(320, 1)
     tall_bf16x3_kernel(const __grid_constant__ CUtensorMap tmA, const TallArgs a) {
-    using Cfg = X3Cfg<NP>;
+    using Cfg = X3Cfg<NP, U>;
     extern __shared__ __align__(1024) unsigned char smem[];
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem + Cfg::OFF_BAR);
     uint64_t *full = bar;             // [kS] FP32 A + B chunk landed
@@ -166,8 +172,14 @@ __global__ void __launch_bounds__(320, 1)
     const int lane = threadIdx.x % 32;
     const int64_t total = a.slabs * a.splits;
 
+    // U: offset within 16 bytes of element (i0, p) of A is (abase + p * ldv) mod 4
+    // (slabs start at multiples of 4 rows), so column q of a stage (which starts
+    // at a multiple of 64) is at doff[q % 4]
+    const int abase = (int)((reinterpret_cast<uintptr_t>(a.A) / sizeof(float)) & 3);
+    const int ldv = (int)((uint64_t)a.lda & 3);
+
     if (threadIdx.x == 0) {
-        prefetch_tmap(&tmA);
+        if (!U) prefetch_tmap(&tmA);
         for (int s = 0; s < kS; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&conv[s], 4);
@@ -196,7 +208,7 @@ __global__ void __launch_bounds__(320, 1)
 
     if (warp == 4) {
         // ------------------------------------------------ producer
-        if (lane == 0) {
+        if (!U && lane == 0) {
             const uint64_t pol_a = policy_evict_first();
             const uint64_t pol_b = policy_evict_last();
             const unsigned char *Bp = static_cast<const unsigned char *>(a.Bp);
@@ -221,6 +233,71 @@ __global__ void __launch_bounds__(320, 1)
                                 &full[s], pol_a);
                     bulk_load(smem + Cfg::OFF_B + s * Cfg::B_BYTES, Bp + (kk / kKB) * Cfg::B_BYTES,
                               Cfg::B_BYTES, &full[s], pol_b);
+                }
+            }
+        } else if (U) {
+            // every lane moves columns lane and lane + 32 of each stage into their
+            // slots, each with one bulk copy of the 16-byte-aligned span around its
+            // rows (column_span_bytes); lane 0 posts the stage's bytes with its
+            // arrival before any copy is issued; columns beyond k are zero-filled,
+            // like the tensor copy's out-of-range fill; rows beyond m hold whatever
+            // the span left (their results are never stored)
+            const uint64_t pol_a = policy_evict_first();
+            const uint64_t pol_b = policy_evict_last();
+            const unsigned char *Bp = static_cast<const unsigned char *>(a.Bp);
+            const float *A = static_cast<const float *>(a.A);
+            int64_t g = 0;
+            bool ok = true;
+            for (int64_t item = blockIdx.x; item < total && ok; item += gridDim.x) {
+                int64_t slab, sp;
+                udivmod(item, a.splits, slab, sp);
+                const int64_t k0 = sp * a.kchunk;
+                const int64_t k1 = (k0 + a.kchunk < a.kp) ? k0 + a.kchunk : a.kp;
+                const int64_t i0 = slab * kBM;
+                const int rows = (int)((a.m - i0 < kBM) ? a.m - i0 : kBM);
+                for (int64_t kk = k0; kk < k1; kk += kKB, ++g) {
+                    const int s = (int)(g % kS);
+                    if (g >= kS) {
+                        const bool got = mbar_wait_bounded(&empty[s], (uint32_t)((g / kS) & 1) ^ 1);
+                        if (!__all_sync(0xffffffffu, got)) {
+                            if (lane == 0) atomicOr(a.status, kDevErrTimeout);
+                            ok = false;
+                            break;
+                        }
+                    }
+                    float *stageA = reinterpret_cast<float *>(smem + s * Cfg::A_BYTES);
+                    uint32_t bytes[kKB / 32];
+                    int dd[kKB / 32];
+                    uint32_t sum = 0;
+#pragma unroll
+                    for (int h = 0; h < kKB / 32; ++h) {
+                        const int q = lane + 32 * h;
+                        const int64_t p = kk + q;
+                        dd[h] = (abase + (int)(p & 3) * ldv) & 3;  // the column's offset within 16 bytes
+                        bytes[h] = p < a.k ? column_span_bytes<float>(rows, dd[h]) : 0u;
+                        if (p >= a.k) {
+                            float *slot0 = stageA + q * Cfg::A_STRIDE;
+                            for (int r = 0; r < Cfg::A_STRIDE; r += 4)
+                                *reinterpret_cast<uint4 *>(slot0 + r) = make_uint4(0, 0, 0, 0);
+                            fence_proxy_async_smem();  // before later copies into the slot
+                        }
+                        sum += bytes[h];
+                    }
+                    const uint32_t stage_bytes = __reduce_add_sync(0xffffffffu, sum);
+                    __syncwarp();  // the zero stores above precede lane 0's arrival
+                    if (lane == 0) {
+                        mbar_arrive_expect_tx(&full[s], Cfg::B_BYTES + stage_bytes);
+                        bulk_load(smem + Cfg::OFF_B + s * Cfg::B_BYTES, Bp + (kk / kKB) * Cfg::B_BYTES,
+                                  Cfg::B_BYTES, &full[s], pol_b);
+                    }
+                    __syncwarp();
+#pragma unroll
+                    for (int h = 0; h < kKB / 32; ++h) {
+                        const int q = lane + 32 * h;
+                        if (bytes[h] != 0u)
+                            bulk_load(stageA + q * Cfg::A_STRIDE, A + i0 + (kk + q) * a.lda - dd[h], bytes[h],
+                                      &full[s], pol_a);
+                    }
                 }
             }
         }
@@ -301,11 +378,12 @@ __global__ void __launch_bounds__(320, 1)
                 const int s = (int)(g % kS);
                 const bool got = mbar_wait_bounded(&full[s], (uint32_t)((g / kS) & 1));
                 unsigned char *stage = smem + s * Cfg::A_BYTES;
-                const float *src = reinterpret_cast<const float *>(stage);  // [64][128] FP32
+                const float *src = reinterpret_cast<const float *>(stage);  // [64][A_STRIDE] FP32
                 float x[kKB];
                 if (got) {
 #pragma unroll
-                    for (int q = 0; q < kKB; ++q) x[q] = src[q * kBM + r];
+                    for (int q = 0; q < kKB; ++q)
+                        x[q] = U ? src[q * Cfg::A_STRIDE + ((abase + (q & 3) * ldv) & 3) + r] : src[q * kBM + r];
                 } else if (lane == 0) {
                     atomicOr(conv_abort, 1u);
                 }
@@ -453,28 +531,33 @@ __global__ void __launch_bounds__(320, 1)
     named_barrier(2, 160);  // with warp 5, before it frees TMEM
 }
 
-template <int NP>
+template <int NP, bool U>
 static cudaError_t launch_x3_t(const CUtensorMap *tmap, const TallArgs &a, int num_sms, cudaStream_t s) {
-    using Cfg = X3Cfg<NP>;
+    using Cfg = X3Cfg<NP, U>;
     {
         const cudaError_t e =
-            ensure_smem_limit(reinterpret_cast<const void *>(tall_bf16x3_kernel<NP>), Cfg::SMEM);
+            ensure_smem_limit(reinterpret_cast<const void *>(tall_bf16x3_kernel<NP, U>), Cfg::SMEM);
         if (e != cudaSuccess) return e;
     }
     const int64_t items = a.slabs * a.splits;
     const int64_t slots = num_sms > 0 ? num_sms : 1;
     const unsigned grid = (unsigned)(items < slots ? items : slots);
     if (grid == 0) return cudaSuccess;
-    tall_bf16x3_kernel<NP><<<grid, Cfg::THREADS, Cfg::SMEM, s>>>(*tmap, a);
+    CUtensorMap none;
+    std::memset(&none, 0, sizeof(none));  // U: never read
+    tall_bf16x3_kernel<NP, U><<<grid, Cfg::THREADS, Cfg::SMEM, s>>>(U ? none : *tmap, a);
     return cudaGetLastError();
 }
 
+// tmap: the tensor map of A, or nullptr for an A that one cannot describe
+// (4-byte aligned; moved column by column).
 cudaError_t launch_tall_bf16x3(int np, const CUtensorMap *tmap, const TallArgs &a, int num_sms,
                                cudaStream_t s) {
+    const bool u = tmap == nullptr;
     switch (np) {
-        case 16: return launch_x3_t<16>(tmap, a, num_sms, s);
-        case 32: return launch_x3_t<32>(tmap, a, num_sms, s);
-        case 64: return launch_x3_t<64>(tmap, a, num_sms, s);
+        case 16: return u ? launch_x3_t<16, true>(tmap, a, num_sms, s) : launch_x3_t<16, false>(tmap, a, num_sms, s);
+        case 32: return u ? launch_x3_t<32, true>(tmap, a, num_sms, s) : launch_x3_t<32, false>(tmap, a, num_sms, s);
+        case 64: return u ? launch_x3_t<64, true>(tmap, a, num_sms, s) : launch_x3_t<64, false>(tmap, a, num_sms, s);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -549,18 +632,6 @@ struct RX3Cfg {
     static_assert(NBAR * 8 + 32 <= OFF_A, "barrier area");
     static_assert(SMEM <= 227 * 1024, "shared memory");
 };
-
-__device__ __forceinline__ void cp_async4(void *smem_dst, const void *gsrc, uint32_t src_bytes) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(smem_addr(smem_dst)),
-                 "l"(reinterpret_cast<uint64_t>(gsrc)), "r"(src_bytes)
-                 : "memory");
-}
-
-// Arrive on `bar` once every earlier cp.async of this thread has landed (the
-// barrier's expected count includes this arrival).
-__device__ __forceinline__ void cp_async_mbar_arrive(uint64_t *bar) {
-    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_addr(bar)) : "memory");
-}
 
 // 2-D tiled tensor copy shared -> global (out-of-range parts of the box are
 // not written); tracked by this thread's bulk async-groups.
@@ -757,9 +828,9 @@ __global__ void __launch_bounds__(512, 1)
                             const int64_t row = mt * kBM + (e & (kBM - 1));
                             const int64_t col = col0 + e / kBM;
                             const bool in = row < a.m && col < a.n;
-                            cp_async4(slot + e, in ? C + row + col * a.ldc : C, in ? 4u : 0u);
+                            cp_async_elem(slot + e, in ? C + row + col * a.ldc : C, in, 4);
                         }
-                        cp_async_mbar_arrive(&c_full[st]);
+                        cp_async_arrive_noinc(&c_full[st]);
                     }
                 }
             }

@@ -51,6 +51,24 @@ __device__ __forceinline__ void fence_proxy_async_smem() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.expect_tx.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+// Element copy global -> shared; a zero source size writes zeros and reads nothing.
+__device__ __forceinline__ void cp_async_elem(void *smem_dst, const void *gsrc, bool valid, int bytes) {
+    const uint32_t n = valid ? (uint32_t)bytes : 0u;
+    if (bytes == 8)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(smem_addr(smem_dst)), "l"(gsrc), "r"(n)
+                     : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(smem_addr(smem_dst)), "l"(gsrc), "r"(n)
+                     : "memory");
+}
+// The barrier counts this thread's arrival once all its earlier cp.async copies have landed.
+__device__ __forceinline__ void cp_async_arrive_noinc(uint64_t *bar) {
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
 // A consumer's release of a shared-memory buffer that a tensor or bulk copy
 // (the async proxy) refills: its reads of the buffer (generic proxy) are
 // ordered before that copy by this fence, issued by every reading thread before
@@ -133,6 +151,19 @@ __device__ __forceinline__ void bulk_load(void *smem_dst, const void *gsrc, uint
         " [%0], [%1], %2, [%3], %4;" ::"r"(smem_addr(smem_dst)),
         "l"(reinterpret_cast<uint64_t>(gsrc)), "r"(bytes), "r"(smem_addr(bar)), "l"(policy)
         : "memory");
+}
+
+// One column of A whose first element sits d elements past a 16-byte boundary,
+// as one bulk copy of the 16-byte-aligned span around its rows [0, rows): from
+// (first element - d) to the next 16-byte boundary after the last row, so row r
+// lands at slot[d + r] of a 16-byte-aligned slot.  The span's extra bytes (under
+// 16 on either side) lie in the same 16-byte chunks as the column's own
+// elements, hence on the same pages (they cannot fault), and land in slot
+// positions that hold no row.  Returns the copy's size.
+template <typename T>
+__device__ __forceinline__ uint32_t column_span_bytes(int rows, int d) {
+    constexpr int V = 16 / (int)sizeof(T);
+    return (uint32_t)((d + rows + V - 1) / V * 16);
 }
 
 __device__ __forceinline__ void prefetch_tmap(const void *tmap) {

@@ -413,40 +413,16 @@ __global__ void __launch_bounds__(TallCfg<T, NP>::THREADS, TallCfg<T, NP>::RESID
 // for a column-major A with lda = m and m not a multiple of 4 -- most of a
 // random serving mix).  The structure is the TMA kernel's: consumer warps, a
 // producer warp and a ring of mbarrier-guarded stages of BM rows x BKS columns.
-// Each of the producer's 32 lanes moves one column of a stage: a column of A
-// may start at any element address, so it is placed in shared memory at its
-// own offset within 16 bytes (d elements into its slot), its 16-byte-aligned
-// interior moves in one bulk copy (cp.async.bulk, the copy engine of the
-// tensor copy, counted on the stage's barrier in bytes), and its head and tail
-// (under 16 bytes each) by element cp.async copies, whose completion the
-// lane's arrival on the barrier waits for (cp.async.mbarrier.arrive.noinc), so
-// no lane waits on a load; nothing outside the column's rows of A is read.
-// Columns beyond k are zero-filled by copies with a zero source size; rows
-// beyond m are left as they are (their results are never stored).  Consumers
-// read the rows at the column's offset with element loads.  B's packed rows
-// come in one bulk copy per stage.  The thread tiles, reduction and split-K
-// finish are the TMA kernel's.
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
-    asm volatile("mbarrier.expect_tx.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
-}
-// Element copy global -> shared; a zero source size writes zeros and reads nothing.
-__device__ __forceinline__ void cp_async_elem(void *smem_dst, const void *gsrc, bool valid, int bytes) {
-    const uint32_t n = valid ? (uint32_t)bytes : 0u;
-    if (bytes == 8)
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(smem_addr(smem_dst)), "l"(gsrc), "r"(n)
-                     : "memory");
-    else
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(smem_addr(smem_dst)), "l"(gsrc), "r"(n)
-                     : "memory");
-}
-__device__ __forceinline__ void cp_async_zero16(void *smem_dst, const void *gsrc) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, 0;" ::"r"(smem_addr(smem_dst)), "l"(gsrc) : "memory");
-}
-// The barrier counts this thread's arrival once all its earlier cp.async copies have landed.
-__device__ __forceinline__ void cp_async_arrive_noinc(uint64_t *bar) {
-    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_addr(bar)) : "memory");
-}
-
+// Each of the producer's 32 lanes moves one column of a stage with one bulk
+// copy (cp.async.bulk, the tensor copy's engine): a column of A may start at
+// any element address, so it is copied together with the 16-byte-aligned span
+// around its rows (column_span_bytes) and sits in shared memory at its own
+// offset within 16 bytes (d elements into its slot).  Lane 0 posts the bytes of
+// the whole stage with its arrival before any lane issues its copy.  Columns
+// beyond k are zero-filled; rows beyond m hold whatever the span or an earlier
+// stage left (their results are never stored).  Consumers read the rows at the
+// column's offset.  B's packed rows come in one bulk copy per stage.  The thread
+// tiles, reduction and split-K finish are the TMA kernel's.
 template <typename T, int NP>
 struct AsyncCfg {
     using Cfg = TallCfg<T, NP>;
@@ -541,7 +517,7 @@ __device__ __forceinline__ void tall_async_block(const TallArgs &a, int64_t slab
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) {
-            mbar_init(&full[s], 32);  // the producer warp's lanes
+            mbar_init(&full[s], 1);  // lane 0 of the producer warp
             mbar_init(&empty[s], Cfg::NWARPS);
         }
         *abort_flag = 0u;
@@ -566,33 +542,23 @@ __device__ __forceinline__ void tall_async_block(const TallArgs &a, int64_t slab
             const int64_t kk = k0 + (int64_t)it * Cfg::BKS;
             const int64_t p = kk + lane;
             const int d = col_off(p);
-            T *slot = sA + st * AC::A_STAGE + lane * AC::APAD + d;  // row r at slot[r]
+            T *slot0 = sA + st * AC::A_STAGE + lane * AC::APAD;  // row r at slot0[d + r]
+            const uint32_t bytes = p < a.k ? column_span_bytes<T>(rows, d) : 0u;
+            if (p >= a.k) {
+                // beyond k: zeros, as B's padding (the whole slot)
+                for (int r = 0; r < AC::APAD; r += V) *reinterpret_cast<uint4 *>(slot0 + r) = make_uint4(0, 0, 0, 0);
+                fence_proxy_async_smem();  // before later copies into the slot
+            }
+            // the stage's bytes are expected once, by lane 0's arrival, before any
+            // copy of it is issued; the zero stores above precede that arrival
+            const uint32_t total = __reduce_add_sync(0xffffffffu, bytes);
+            __syncwarp();
             if (lane == 0) {
-                mbar_expect_tx(&full[st], Cfg::B_STAGE * (int)sizeof(T));
+                mbar_arrive_expect_tx(&full[st], Cfg::B_STAGE * (uint32_t)sizeof(T) + total);
                 bulk_load(sB + st * Cfg::B_STAGE, Bp + kk * NP, Cfg::B_STAGE * (int)sizeof(T), &full[st], pol_b);
             }
-            if (p < a.k) {
-                const T *col = A + i0 + p * a.lda;
-                const int head = (V - d) & (V - 1);        // rows before the first 16-byte boundary
-                const int h = head < rows ? head : rows;
-                const int nb = (rows - h) / V;              // whole 16-byte chunks inside the rows
-                const int tail0 = h + nb * V;
-                if (nb > 0) {
-                    mbar_expect_tx(&full[st], (uint32_t)(nb * 16));
-                    bulk_load(slot + h, col + h, (uint32_t)(nb * 16), &full[st], pol_a);
-                }
-#pragma unroll
-                for (int r = 0; r < V; ++r)
-                    if (r < h) cp_async_elem(slot + r, col + r, true, (int)sizeof(T));
-#pragma unroll
-                for (int r = 0; r < V; ++r)
-                    if (tail0 + r < rows) cp_async_elem(slot + tail0 + r, col + tail0 + r, true, (int)sizeof(T));
-            } else {
-                // beyond k: zeros, as B's padding (the whole slot, 16 bytes at a time)
-                T *slot0 = sA + st * AC::A_STAGE + lane * AC::APAD;
-                for (int r = 0; r < AC::APAD; r += V) cp_async_zero16(slot0 + r, Bp);  // 16-byte aligned source, not read
-            }
-            cp_async_arrive_noinc(&full[st]);  // this lane's arrival, once its element copies have landed
+            __syncwarp();
+            if (p < a.k) bulk_load(slot0, A + i0 + p * a.lda - d, bytes, &full[st], pol_a);
         }
         return;
     }

@@ -90,11 +90,45 @@ def test_bf16x3_errors():
     with pytest.raises(tsmm.TsmmError) as e:  # FP64 has no BF16x3 mode
         tsmm.plan(50, 16, 100, torch.float64, precision=X3)
     assert e.value.status == 1
-    pb = tsmm.pack_b(B, precision=X3)
-    A_odd = to_device(ti.matrix_np(50, 100, 1, "uniform", np.float32), offset=1)
-    with pytest.raises(tsmm.TsmmError) as e:  # TMA-only mode: unaligned A
-        tsmm.execute(pl_x3, 1.0, A_odd, pb, 0.0, C)
+    # regime (ii) in this mode streams A with TMA only: an A at an odd offset is refused
+    Bk = to_device(ti.matrix_np(40, 130, 2, "uniform", np.float32))
+    pb_rk = tsmm.pack_b(Bk, precision=X3)
+    pl_rk = tsmm.plan(300, 130, 40, torch.float32, precision=X3)
+    A_odd = to_device(ti.matrix_np(300, 40, 1, "uniform", np.float32), offset=1)
+    C_rk = to_device(np.zeros((300, 130), np.float32, order="F"))
+    with pytest.raises(tsmm.TsmmError) as e:
+        tsmm.execute(pl_rk, 1.0, A_odd, pb_rk, 0.0, C_rk)
     assert e.value.status == 4
+
+
+@pytest.mark.parametrize("m,n,k,pad,offset", [(1000, 64, 777, 1, 0), (300, 16, 20000, 2, 1), (257, 40, 130, 3, 3),
+                                              (2050, 32, 4000, 1, 2), (129, 17, 64, 0, 1), (5, 3, 1, 1, 1),
+                                              # several work items per persistent block, with split-K
+                                              (20000, 64, 4000, 3, 0), (40001, 32, 70, 2, 0)])
+def test_bf16x3_unaligned_A_equals_aligned(m, n, k, pad, offset):
+    """Regime (i) with an A that a tensor map cannot describe (lda*4 or the base
+    not a multiple of 16 bytes): its columns are copied one by one into padded
+    slots and read at their offsets, then split and multiplied exactly as the
+    tensor-copy path does, so the result equals that path's on the same values
+    bit for bit (and the mode bound holds against the oracle)."""
+    A = ti.matrix_np(m, k, 51, "uniform", np.float32)
+    B = ti.matrix_np(k, n, 52, "uniform", np.float32)
+    C0 = ti.matrix_np(m, n, 53, "uniform", np.float32)
+    ref, _ = run_x3(A, B, C0, 1.25, 0.5)  # lda rounded up to 4, base aligned: tensor copies
+    C, _ = run_x3(A, B, C0, 1.25, 0.5, lda=m + pad, a_offset=offset)
+    assert np.array_equal(C, ref)
+    Cref, _ = oracle.tsmm(1.25, A, B, 0.5, C0)
+    assert np.all(np.abs(C.astype(np.float64) - Cref) <= x3_bound(A, B, C0, 1.25, 0.5))
+
+
+@pytest.mark.parametrize("m,n,k,pad,offset", [(1003, 64, 777, 1, 0), (258, 40, 130, 3, 2)])
+def test_bf16x3_unaligned_A_integer_bit_exact(m, n, k, pad, offset):
+    A = ti.matrix_np(m, k, 61, "integer", np.float32)
+    B = ti.matrix_np(k, n, 62, "integer", np.float32)
+    C0 = ti.matrix_np(m, n, 63, "integer", np.float32)
+    C, _ = run_x3(A, B, C0, 1.5, 0.5, lda=m + pad, a_offset=offset)
+    Cref, _ = oracle.tsmm(1.5, A, B, 0.5, C0)
+    np.testing.assert_array_equal(C, oracle.round_to(Cref, np.float32))
 
 
 def test_bf16x3_pack_layout_roundtrip():

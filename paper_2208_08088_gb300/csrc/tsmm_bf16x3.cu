@@ -111,8 +111,15 @@ struct X3Cfg {
     static constexpr int NBAR = 3 * kS + 4 + 1;
     static constexpr int SMEM = OFF_BAR + NBAR * 8 + 32;
     static constexpr int TMEM_COLS = 2 * NP < 32 ? 32 : 2 * NP;  // double-buffered accumulator
-    static constexpr int THREADS = 320;
+    // U: three producer warps (4, 10, 11), each moving up to 22 of a stage's 64
+    // columns, one per lane: one warp issues its column copies too slowly to
+    // keep up with HBM (one: 0.31 of HBM, two: 0.54); 12 warps still fit 168
+    // registers a thread
+    static constexpr int PRODUCERS = U ? 3 : 1;
+    static constexpr int COLS_PER_PRODUCER = (kKB + PRODUCERS - 1) / PRODUCERS;
+    static constexpr int THREADS = 320 + 32 * (PRODUCERS - 1);
     static_assert(SMEM <= 227 * 1024, "shared memory");
+    static_assert(!U || COLS_PER_PRODUCER <= 32, "one column per producer lane");
 };
 
 }  // namespace
@@ -151,7 +158,7 @@ __global__ void pack_b_bf16x3_kernel(const float *__restrict__ B, int64_t k, int
 // epilogue warps, so the MMAs of the next item run while the previous item's
 // results are stored; the producer and converter rings run across items.
 template <int NP, bool U>
-__global__ void __launch_bounds__(320, 1)
+__global__ void __launch_bounds__(X3Cfg<NP, U>::THREADS, 1)
     tall_bf16x3_kernel(const __grid_constant__ CUtensorMap tmA, const TallArgs a) {
     using Cfg = X3Cfg<NP, U>;
     extern __shared__ __align__(1024) unsigned char smem[];
@@ -181,7 +188,7 @@ __global__ void __launch_bounds__(320, 1)
     if (threadIdx.x == 0) {
         if (!U) prefetch_tmap(&tmA);
         for (int s = 0; s < kS; ++s) {
-            mbar_init(&full[s], 1);
+            mbar_init(&full[s], Cfg::PRODUCERS);  // lane 0 of each producer warp
             mbar_init(&conv[s], 4);
             mbar_init(&empty[s], 1);
         }
@@ -206,8 +213,8 @@ __global__ void __launch_bounds__(320, 1)
     tc_fence_after();
     const uint32_t tmem = *tslot;
 
-    if (warp == 4) {
-        // ------------------------------------------------ producer
+    if (warp == 4 || (U && warp >= 10)) {
+        // ------------------------------------------------ producer(s)
         if (!U && lane == 0) {
             const uint64_t pol_a = policy_evict_first();
             const uint64_t pol_b = policy_evict_last();
@@ -236,12 +243,14 @@ __global__ void __launch_bounds__(320, 1)
                 }
             }
         } else if (U) {
-            // every lane moves columns lane and lane + 32 of each stage into their
-            // slots, each with one bulk copy of the 16-byte-aligned span around its
-            // rows (column_span_bytes); lane 0 posts the stage's bytes with its
-            // arrival before any copy is issued; columns beyond k are zero-filled,
-            // like the tensor copy's out-of-range fill; rows beyond m hold whatever
-            // the span left (their results are never stored)
+            // lane l < COLS_PER_PRODUCER of producer w moves column
+            // w * COLS_PER_PRODUCER + l of each stage into its slot with one bulk copy of the 16-byte-aligned span around its rows
+            // (column_span_bytes); lane 0 of each producer warp posts its warp's
+            // bytes (and warp 4 the B chunk's) with its arrival before any of its
+            // copies is issued; columns beyond k are zero-filled, like the tensor
+            // copy's out-of-range fill; rows beyond m hold whatever the span left
+            // (their results are never stored)
+            const int pw = warp == 4 ? 0 : warp - 9;  // 0, 1, 2
             const uint64_t pol_a = policy_evict_first();
             const uint64_t pol_b = policy_evict_last();
             const unsigned char *Bp = static_cast<const unsigned char *>(a.Bp);
@@ -266,38 +275,27 @@ __global__ void __launch_bounds__(320, 1)
                         }
                     }
                     float *stageA = reinterpret_cast<float *>(smem + s * Cfg::A_BYTES);
-                    uint32_t bytes[kKB / 32];
-                    int dd[kKB / 32];
-                    uint32_t sum = 0;
-#pragma unroll
-                    for (int h = 0; h < kKB / 32; ++h) {
-                        const int q = lane + 32 * h;
-                        const int64_t p = kk + q;
-                        dd[h] = (abase + (int)(p & 3) * ldv) & 3;  // the column's offset within 16 bytes
-                        bytes[h] = p < a.k ? column_span_bytes<float>(rows, dd[h]) : 0u;
-                        if (p >= a.k) {
-                            float *slot0 = stageA + q * Cfg::A_STRIDE;
-                            for (int r = 0; r < Cfg::A_STRIDE; r += 4)
-                                *reinterpret_cast<uint4 *>(slot0 + r) = make_uint4(0, 0, 0, 0);
-                            fence_proxy_async_smem();  // before later copies into the slot
-                        }
-                        sum += bytes[h];
+                    const int q = Cfg::COLS_PER_PRODUCER * pw + lane;
+                    const bool mine = lane < Cfg::COLS_PER_PRODUCER && q < kKB;
+                    const int64_t p = kk + q;
+                    float *slot0 = stageA + q * Cfg::A_STRIDE;
+                    const int d = (abase + (int)(p & 3) * ldv) & 3;  // the column's offset within 16 bytes
+                    const uint32_t bytes = mine && p < a.k ? column_span_bytes<float>(rows, d) : 0u;
+                    if (mine && p >= a.k) {
+                        for (int r = 0; r < Cfg::A_STRIDE; r += 4)
+                            *reinterpret_cast<uint4 *>(slot0 + r) = make_uint4(0, 0, 0, 0);
+                        fence_proxy_async_smem();  // before later copies into the slot
                     }
-                    const uint32_t stage_bytes = __reduce_add_sync(0xffffffffu, sum);
+                    const uint32_t warp_bytes = __reduce_add_sync(0xffffffffu, bytes);
                     __syncwarp();  // the zero stores above precede lane 0's arrival
                     if (lane == 0) {
-                        mbar_arrive_expect_tx(&full[s], Cfg::B_BYTES + stage_bytes);
-                        bulk_load(smem + Cfg::OFF_B + s * Cfg::B_BYTES, Bp + (kk / kKB) * Cfg::B_BYTES,
-                                  Cfg::B_BYTES, &full[s], pol_b);
+                        mbar_arrive_expect_tx(&full[s], (pw == 0 ? Cfg::B_BYTES : 0u) + warp_bytes);
+                        if (pw == 0)
+                            bulk_load(smem + Cfg::OFF_B + s * Cfg::B_BYTES, Bp + (kk / kKB) * Cfg::B_BYTES,
+                                      Cfg::B_BYTES, &full[s], pol_b);
                     }
                     __syncwarp();
-#pragma unroll
-                    for (int h = 0; h < kKB / 32; ++h) {
-                        const int q = lane + 32 * h;
-                        if (bytes[h] != 0u)
-                            bulk_load(stageA + q * Cfg::A_STRIDE, A + i0 + (kk + q) * a.lda - dd[h], bytes[h],
-                                      &full[s], pol_a);
-                    }
+                    if (bytes != 0u) bulk_load(slot0, A + i0 + p * a.lda - d, bytes, &full[s], pol_a);
                 }
             }
         }

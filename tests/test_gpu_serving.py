@@ -87,6 +87,28 @@ def test_serving_same_alone_and_in_mix():
         assert c["arrival_s"] <= c["admit_s"] <= c["launch_s"] <= c["complete_s"]
 
 
+def test_serving_fp64_same_alone_and_in_mix():
+    """An FP64 server: every request equal bit for bit alone and in the mix, and
+    within the oracle's componentwise bound (Dot2-accurate reference)."""
+    bs = make_bs(np.float64)
+    reqs = make_requests(bs, 24, seed=7, dtype=np.float64)
+    alone = {}
+    srv = tsmm.Server(budget_bytes=8 << 30, dtype=torch.float64, num_streams=4, max_batch=16)
+    for q in reqs:
+        res, _ = run(srv, bs, [q])
+        alone[q["id"]] = res[q["id"]]
+    srv.close()
+    srv = tsmm.Server(budget_bytes=8 << 30, dtype=torch.float64, num_streams=4, max_batch=16)
+    mix, _ = run(srv, bs, reqs, spread_s=0.01, seed=8)
+    srv.close()
+    for q in reqs:
+        assert np.array_equal(mix[q["id"]], alone[q["id"]]), f"request {q['id']} differs"
+        k, n, B, pb = bs[q["b"]]
+        Cref, E = oracle.tsmm(q["alpha"], q["A"], B, q["beta"], q["C0"] if q["beta"] else None)
+        ok, ratio, nbad = oracle.check(mix[q["id"]], Cref, E, np.float64)
+        assert ok, f"request {q['id']}: {nbad} entries outside the bound"
+
+
 def test_serving_mix_repeats_bitwise_under_concurrency():
     """Eight mixes of the same 40 requests, each with its own arrival order,
     against one direct tsmm_execute per request: every result identical bit

@@ -81,10 +81,9 @@ typedef enum {
  * 3*2^-16 of |A||B| per product, so it does NOT meet the native bound for
  * small k; its documented bound is |C - C_exact| <= (2^-13 + 4*k*2^-24) *
  * (|alpha| sum_p |A[i,p]||B[p,j]| + |beta||C0[i,j]|).  Inf/NaN inputs may turn
- * into NaN (the split of an infinity is Inf - Inf).  Regime (i) takes any A
- * aligned to 4 bytes (an A that a tensor map cannot describe is moved column
- * by column, with the same result); regime (ii) needs a 16-byte aligned A with
- * lda*4 a multiple of 16 (else TSMM_ERR_MISALIGNED).
+ * into NaN (the split of an infinity is Inf - Inf).  Both regimes take any A
+ * aligned to 4 bytes: an A that a tensor map cannot describe (base or lda*4
+ * not a multiple of 16) is moved column by column, with the same result.
  */
 typedef enum { TSMM_PREC_NATIVE = 0, TSMM_PREC_BF16X3 = 1 } tsmm_precision;
 

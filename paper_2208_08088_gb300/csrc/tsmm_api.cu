@@ -470,7 +470,6 @@ tsmm_status tsmm_execute(tsmm_plan_t p, double alpha, const void *A_dev, int64_t
     }
     if (p->precision == TSMM_PREC_BF16X3) {
         if (p->regime == 2) {
-            if (!tma) return TSMM_ERR_MISALIGNED;  // regime (ii) in this mode streams A with TMA only
             RankArgs ra;
             ra.m = m;
             ra.n = n;
@@ -490,7 +489,9 @@ tsmm_status tsmm_execute(tsmm_plan_t p, double alpha, const void *A_dev, int64_t
                 const tsmm_status st = encode_tmapc(p, C_dev, m, n, ldc, es, kX3RankSub);
                 if (st != TSMM_OK) return st;
             }
-            return cuda_status(launch_rankk_bf16x3(&p->tmap, tmc ? &p->tmapc : nullptr, ra, p->status, s));
+            // an A that a tensor map cannot describe is moved column by column
+            return cuda_status(
+                launch_rankk_bf16x3(tma ? &p->tmap : nullptr, tmc ? &p->tmapc : nullptr, ra, p->status, s));
         }
         // regime (i): an A that a tensor map cannot describe is moved column by column
         return cuda_status(launch_tall_bf16x3(p->np, tma ? &p->tmap : nullptr, a, p->num_sms, s));

@@ -604,14 +604,20 @@ constexpr int kRNCHMax = 16;       // n-tiles per work item, at most
 constexpr int kRSUB = kX3RankSub;  // columns per sub-tile (TMA box 128 x 32 FP32 = 16 KB)
 constexpr int kRSUBS = kX3RankNT / kRSUB;
 
-template <int KC>  // 64-column k chunks: 1 (k <= 64) or 2 (k <= 128)
+// U: an A that a tensor map cannot describe; each FP32 column of the A tile
+// then sits in a slot of A_STRIDE rows at its own offset within 16 bytes (one
+// B buffer fewer at KC = 2 makes room).
+template <int KC, bool U = false>  // 64-column k chunks: 1 (k <= 64) or 2 (k <= 128)
 struct RX3Cfg {
     static constexpr int NT = kX3RankNT;               // 128 columns per tile
-    static constexpr int A_BYTES = KC * kBM * kKB * 4; // FP32 in, then hi|lo per chunk, in place
+    static constexpr int A_STRIDE = U ? kBM + 8 : kBM; // FP32 elements per column slot
+    // one 64-column chunk: FP32 in, then hi|lo (32 KB) over its start, in place; whole KB
+    static constexpr int A_CHUNK_BYTES = (kKB * A_STRIDE * 4 + 1023) / 1024 * 1024;
+    static constexpr int A_BYTES = KC * A_CHUNK_BYTES;
     static constexpr int B_CHUNK = 2 * NT * kKB * 2;   // hi|lo of one 64-k chunk of one tile
     static constexpr int B_TILE = KC * B_CHUNK;
-    static constexpr int NB = KC == 1 ? 2 : 3;         // B chunk buffers
-    static constexpr int CS = KC == 1 ? 8 : 4;         // C slots
+    static constexpr int NB = (KC == 1 || U) ? 2 : 3;  // B chunk buffers
+    static constexpr int CS = (KC == 1 && !U) ? 8 : 4; // C slots (U, KC = 1: 8 do not fit)
     // Slot q % CS must always serve the same epilogue half (sub-tile q % 4):
     // its consumers then meet its phases in order, so parity waits cannot
     // alias (a half two phases ahead of a slot shared with the other half
@@ -683,11 +689,11 @@ __device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity) {
 
 }  // namespace
 
-template <int KC>
+template <int KC, bool U>
 __global__ void __launch_bounds__(512, 1)
     rankk_bf16x3_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmC,
                         const RankArgs a, unsigned *status, int c_tma, int rnch, int lag) {
-    using Cfg = RX3Cfg<KC>;
+    using Cfg = RX3Cfg<KC, U>;
     constexpr int NT = Cfg::NT;
     constexpr int NB = Cfg::NB;
     constexpr int CS = Cfg::CS;
@@ -716,8 +722,13 @@ __global__ void __launch_bounds__(512, 1)
     const int64_t total = mtiles * nch;
     const bool use_c0 = a.beta != 0.0;
 
+    // U: offset within 16 bytes of element (i0, p) of A is (abase + p * ldv) mod 4
+    // (tiles start at multiples of 4 rows, chunks at multiples of 64 columns)
+    const int abase = (int)((reinterpret_cast<uintptr_t>(a.A) / sizeof(float)) & 3);
+    const int ldv = (int)((uint64_t)a.lda & 3);
+
     if (threadIdx.x == 0) {
-        prefetch_tmap(&tmA);
+        if (!U) prefetch_tmap(&tmA);
         if (c_tma) prefetch_tmap(&tmC);
         mbar_init(a_full, 1);
         mbar_init(a_conv, 4);
@@ -752,10 +763,18 @@ __global__ void __launch_bounds__(512, 1)
 
     if (warp == 4) {
         // ------------------------------------------------ producer: A and B
-        if (lane == 0) {
+        // A by tensor copies from lane 0, or (U) every lane moving columns lane,
+        // lane + 32, ... of the item's A tile into their slots, each with one bulk
+        // copy of the 16-byte-aligned span around its rows (column_span_bytes);
+        // lane 0 posts the tile's bytes with its arrival before any copy is
+        // issued, columns from k to the tile's end are zero-filled (the tensor
+        // copy's out-of-range fill) and rows beyond m hold whatever the span left
+        // (their results are never stored).  B chunks by bulk copies from lane 0.
+        if (lane == 0 || U) {
             const uint64_t pol_a = policy_evict_last();  // A tiles are re-read by other n-chunks
             const uint64_t pol_b = policy_evict_last();
             const unsigned char *Bp = static_cast<const unsigned char *>(a.Bp);
+            const float *A = static_cast<const float *>(a.A);
             int64_t gq = 0;  // B chunks issued
             int j = 0;
             bool ok = true;
@@ -764,32 +783,77 @@ __global__ void __launch_bounds__(512, 1)
                 udivmod(item, nch, mt, ch);
                 const int64_t t0 = ch * rnch;
                 const int64_t t1 = (t0 + rnch < ntiles) ? t0 + rnch : ntiles;
-                if (j >= 1 && !mbar_wait_bounded(a_empty, (uint32_t)((j - 1) & 1))) {
-                    ok = false;
-                    break;
-                }
-                mbar_arrive_expect_tx(a_full, Cfg::A_BYTES);
-                for (int box = 0; box < 2 * KC; ++box)
-                    tma_load_2d(smem + Cfg::OFF_A + box * (kBM * 32 * 4), &tmA, (int32_t)(mt * kBM),
-                                (int32_t)(box * 32), a_full, pol_a);
-                for (int64_t t = t0; t < t1 && ok; ++t) {
-                    for (int c = 0; c < KC; ++c, ++gq) {
-                        const int sb = (int)(gq % NB);
-                        if (gq >= NB && !mbar_wait_bounded(&b_empty[sb], (uint32_t)((gq / NB) & 1) ^ 1)) {
-                            ok = false;
-                            break;
-                        }
-                        mbar_arrive_expect_tx(&b_full[sb], Cfg::B_CHUNK);
-                        bulk_load(smem + Cfg::OFF_B + sb * Cfg::B_CHUNK,
-                                  Bp + t * Cfg::B_TILE + c * Cfg::B_CHUNK, Cfg::B_CHUNK, &b_full[sb], pol_b);
+                if (j >= 1) {
+                    bool got = mbar_wait_bounded(a_empty, (uint32_t)((j - 1) & 1));
+                    if (U) got = __all_sync(0xffffffffu, got);
+                    if (!got) {
+                        ok = false;
+                        break;
                     }
                 }
+                if constexpr (!U) {
+                    mbar_arrive_expect_tx(a_full, Cfg::A_BYTES);
+                    for (int box = 0; box < 2 * KC; ++box)
+                        tma_load_2d(smem + Cfg::OFF_A + box * (kBM * 32 * 4), &tmA, (int32_t)(mt * kBM),
+                                    (int32_t)(box * 32), a_full, pol_a);
+                } else {
+                    const int64_t i0 = mt * kBM;
+                    const int rows = (int)((a.m - i0 < kBM) ? a.m - i0 : kBM);
+                    constexpr int PER_LANE = KC * kKB / 32;
+                    uint32_t bytes[PER_LANE];
+                    int dd[PER_LANE];
+                    uint32_t sum = 0;
+#pragma unroll
+                    for (int h = 0; h < PER_LANE; ++h) {
+                        const int p = lane + 32 * h;  // column of the tile
+                        float *slot0 = reinterpret_cast<float *>(smem + Cfg::OFF_A + (p / kKB) * Cfg::A_CHUNK_BYTES) +
+                                       (p % kKB) * Cfg::A_STRIDE;
+                        dd[h] = (abase + (p & 3) * ldv) & 3;  // the column's offset within 16 bytes
+                        bytes[h] = p < a.k ? column_span_bytes<float>(rows, dd[h]) : 0u;
+                        if (p >= a.k) {
+                            for (int r = 0; r < Cfg::A_STRIDE; r += 4)
+                                *reinterpret_cast<uint4 *>(slot0 + r) = make_uint4(0, 0, 0, 0);
+                            fence_proxy_async_smem();  // before later copies into the slot
+                        }
+                        sum += bytes[h];
+                    }
+                    const uint32_t tile_bytes = __reduce_add_sync(0xffffffffu, sum);
+                    __syncwarp();  // the zero stores above precede lane 0's arrival
+                    if (lane == 0) mbar_arrive_expect_tx(a_full, tile_bytes);
+                    __syncwarp();
+#pragma unroll
+                    for (int h = 0; h < PER_LANE; ++h) {
+                        const int p = lane + 32 * h;
+                        if (bytes[h] != 0u)
+                            bulk_load(reinterpret_cast<float *>(smem + Cfg::OFF_A + (p / kKB) * Cfg::A_CHUNK_BYTES) +
+                                          (p % kKB) * Cfg::A_STRIDE,
+                                      A + i0 + (int64_t)p * a.lda - dd[h], bytes[h], a_full, pol_a);
+                    }
+                }
+                if (lane == 0) {
+                    for (int64_t t = t0; t < t1 && ok; ++t) {
+                        for (int c = 0; c < KC; ++c, ++gq) {
+                            const int sb = (int)(gq % NB);
+                            if (gq >= NB &&
+                                !mbar_wait_bounded(&b_empty[sb], (uint32_t)((gq / NB) & 1) ^ 1)) {
+                                ok = false;
+                                break;
+                            }
+                            mbar_arrive_expect_tx(&b_full[sb], Cfg::B_CHUNK);
+                            bulk_load(smem + Cfg::OFF_B + sb * Cfg::B_CHUNK,
+                                      Bp + t * Cfg::B_TILE + c * Cfg::B_CHUNK, Cfg::B_CHUNK, &b_full[sb], pol_b);
+                        }
+                    }
+                }
+                if (U) ok = __shfl_sync(0xffffffffu, ok, 0);
             }
-            if (!ok) atomicOr(status, kDevErrTimeout);
-            // copies still in flight land before the block may exit
-            if (j >= 1) mbar_wait_bounded(a_full, (uint32_t)((j - 1) & 1));
-            for (int64_t q = gq > NB ? gq - NB : 0; q < gq; ++q)
-                mbar_wait_bounded(&b_full[q % NB], (uint32_t)((q / NB) & 1));
+            if (lane == 0) {
+                if (!ok) atomicOr(status, kDevErrTimeout);
+                // copies still in flight land before the block may exit
+                if (j >= 1) mbar_wait_bounded(a_full, (uint32_t)((j - 1) & 1));
+                for (int64_t q = gq > NB ? gq - NB : 0; q < gq; ++q)
+                    mbar_wait_bounded(&b_full[q % NB], (uint32_t)((q / NB) & 1));
+            }
         }
         return;
     }
@@ -908,7 +972,7 @@ __global__ void __launch_bounds__(512, 1)
                             break;
                         }
                         tc_fence_after();
-                        const uint32_t ahi = smem_addr(smem + Cfg::OFF_A + c * (kBM * kKB * 4));
+                        const uint32_t ahi = smem_addr(smem + Cfg::OFF_A + c * Cfg::A_CHUNK_BYTES);
                         const uint32_t alo = ahi + kBM * kKB * 2;
                         const uint32_t bhi = smem_addr(smem + Cfg::OFF_B + sb * Cfg::B_CHUNK);
                         const uint32_t blo = bhi + NT * kKB * 2;
@@ -955,11 +1019,12 @@ __global__ void __launch_bounds__(512, 1)
             }
 #pragma unroll
             for (int c = 0; c < KC; ++c) {
-                unsigned char *stage = smem + Cfg::OFF_A + c * (kBM * kKB * 4);
-                const float *src = reinterpret_cast<const float *>(stage);  // [64][128] FP32
+                unsigned char *stage = smem + Cfg::OFF_A + c * Cfg::A_CHUNK_BYTES;
+                const float *src = reinterpret_cast<const float *>(stage);  // [64][A_STRIDE] FP32
                 float x[kKB];
 #pragma unroll
-                for (int q = 0; q < kKB; ++q) x[q] = src[q * kBM + r];
+                for (int q = 0; q < kKB; ++q)
+                    x[q] = U ? src[q * Cfg::A_STRIDE + ((abase + (q & 3) * ldv) & 3) + r] : src[q * kBM + r];
                 named_barrier(1, 128);  // the whole chunk is read before it is overwritten
                 unsigned char *hi = stage;
                 unsigned char *lo = stage + kBM * kKB * 2;
@@ -1062,13 +1127,13 @@ __global__ void __launch_bounds__(512, 1)
     named_barrier(2, 288);  // with warp 5, before it frees TMEM
 }
 
-template <int KC>
+template <int KC, bool U>
 static cudaError_t launch_rx3_t(const CUtensorMap *tmA, const CUtensorMap *tmC, const RankArgs &a,
                                 unsigned *status, cudaStream_t s) {
-    using Cfg = RX3Cfg<KC>;
+    using Cfg = RX3Cfg<KC, U>;
     {
         const cudaError_t e =
-            ensure_smem_limit(reinterpret_cast<const void *>(rankk_bf16x3_kernel<KC>), Cfg::SMEM);
+            ensure_smem_limit(reinterpret_cast<const void *>(rankk_bf16x3_kernel<KC, U>), Cfg::SMEM);
         if (e != cudaSuccess) return e;
     }
     const int64_t mtiles = (a.m + kBM - 1) / kBM;
@@ -1085,16 +1150,21 @@ static cudaError_t launch_rx3_t(const CUtensorMap *tmA, const CUtensorMap *tmC, 
     memset(&none, 0, sizeof(none));
     const int smem = (tmC || a.beta != 0.0) ? Cfg::SMEM : Cfg::SMEM_NO_SLOTS;
     // with only 4 slots and C0 to prefetch, free each slot as early as possible
-    const int lag = (KC == 2 && a.beta != 0.0) ? 0 : 1;
-    rankk_bf16x3_kernel<KC><<<grid, Cfg::THREADS, smem, s>>>(*tmA, tmC ? *tmC : none, a, status,
+    const int lag = (Cfg::CS == 4 && a.beta != 0.0) ? 0 : 1;
+    rankk_bf16x3_kernel<KC, U><<<grid, Cfg::THREADS, smem, s>>>(U ? none : *tmA, tmC ? *tmC : none, a, status,
                                                              tmC ? 1 : 0, (int)rnch, lag);
     return cudaGetLastError();
 }
 
+// tmA: the tensor map of A, or nullptr for an A that one cannot describe
+// (4-byte aligned; moved column by column).
 cudaError_t launch_rankk_bf16x3(const CUtensorMap *tmA, const CUtensorMap *tmC, const RankArgs &a,
                                 unsigned *status, cudaStream_t s) {
-    return a.kp <= kKB ? launch_rx3_t<1>(tmA, tmC, a, status, s)
-                       : launch_rx3_t<2>(tmA, tmC, a, status, s);
+    if (tmA == nullptr)
+        return a.kp <= kKB ? launch_rx3_t<1, true>(tmA, tmC, a, status, s)
+                           : launch_rx3_t<2, true>(tmA, tmC, a, status, s);
+    return a.kp <= kKB ? launch_rx3_t<1, false>(tmA, tmC, a, status, s)
+                       : launch_rx3_t<2, false>(tmA, tmC, a, status, s);
 }
 
 }  // namespace tsmm

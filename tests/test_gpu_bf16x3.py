@@ -90,15 +90,6 @@ def test_bf16x3_errors():
     with pytest.raises(tsmm.TsmmError) as e:  # FP64 has no BF16x3 mode
         tsmm.plan(50, 16, 100, torch.float64, precision=X3)
     assert e.value.status == 1
-    # regime (ii) in this mode streams A with TMA only: an A at an odd offset is refused
-    Bk = to_device(ti.matrix_np(40, 130, 2, "uniform", np.float32))
-    pb_rk = tsmm.pack_b(Bk, precision=X3)
-    pl_rk = tsmm.plan(300, 130, 40, torch.float32, precision=X3)
-    A_odd = to_device(ti.matrix_np(300, 40, 1, "uniform", np.float32), offset=1)
-    C_rk = to_device(np.zeros((300, 130), np.float32, order="F"))
-    with pytest.raises(tsmm.TsmmError) as e:
-        tsmm.execute(pl_rk, 1.0, A_odd, pb_rk, 0.0, C_rk)
-    assert e.value.status == 4
 
 
 @pytest.mark.parametrize("m,n,k,pad,offset", [(1000, 64, 777, 1, 0), (300, 16, 20000, 2, 1), (257, 40, 130, 3, 3),
@@ -201,6 +192,36 @@ def test_bf16x3_rankk_integer_bit_exact(m, n, k, beta):
     assert pl.info()["regime"] == 2
     Cref, _ = oracle.tsmm(1.5, A, B, beta, C0 if beta else None)
     np.testing.assert_array_equal(C, oracle.round_to(Cref, np.float32))
+
+
+@pytest.mark.parametrize("m,n,k,pad,offset,beta,ldc_pad", [(1000, 700, 128, 1, 0, 0.5, 0), (257, 300, 40, 3, 2, 0.0, 0),
+                                                             (2050, 130, 96, 2, 1, 1.0, 1), (131, 129, 64, 0, 3, 0.5, 0),
+                                                             (4099, 1000, 17, 1, 1, 0.5, 3)])
+def test_bf16x3_rankk_unaligned_A_equals_aligned(m, n, k, pad, offset, beta, ldc_pad):
+    """Regime (ii) in the tensor-core mode with an A that a tensor map cannot
+    describe: the item's A tile is copied column by column into padded slots
+    and split as the tensor-copy path does, so the result equals that path's on
+    the same values bit for bit, and integer inputs are exact."""
+    for dist, seeds in (("uniform", (71, 72, 73)), ("integer", (74, 75, 76))):
+        A = ti.matrix_np(m, k, seeds[0], dist, np.float32)
+        B = ti.matrix_np(k, n, seeds[1], dist, np.float32)
+        C0 = ti.matrix_np(m, n, seeds[2], dist, np.float32)
+        pb = tsmm.pack_b(to_device(B), precision=X3)
+        pl = tsmm.plan(m, n, k, torch.float32, precision=X3)
+        assert pl.info()["regime"] == 2
+        outs = []
+        for lda, off in (((m + 3) // 4 * 4, 0), (m + pad, offset)):
+            dC = to_device(C0, m + ldc_pad)
+            tsmm.execute(pl, 1.25, to_device(A, lda, off), pb, beta, dC)
+            pl.check()
+            outs.append(dC.cpu().numpy())
+        assert np.array_equal(outs[1], outs[0])
+        Cref, _ = oracle.tsmm(1.25, A, B, beta, C0 if beta else None)
+        if dist == "integer":
+            np.testing.assert_array_equal(outs[1], oracle.round_to(Cref, np.float32))
+        else:
+            E3 = x3_bound(A, B, C0 if beta else None, 1.25, beta)
+            assert np.all(np.abs(outs[1].astype(np.float64) - Cref) <= E3)
 
 
 @pytest.mark.parametrize("beta", [1.5, 0.0])

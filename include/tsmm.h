@@ -203,10 +203,14 @@ TSMM_API tsmm_status tsmm_plan_info(tsmm_plan_t plan, int *regime, int *np, int 
  * written.  A and C must not overlap.  `pb` must have been packed with the
  * plan's (k, n, dtype) on the same device (else TSMM_ERR_MISMATCH).
  *
- * A 16-byte aligned A with lda*sizeof(element) a multiple of 16 takes the
- * TMA-staged kernel; other alignments take a slower kernel with plain loads
- * (pointers must still be aligned to the element size, else MISALIGNED).
- * Enqueues one or two kernels on `stream` and returns.
+ * A 16-byte aligned A with lda*sizeof(element) a multiple of 16 is staged by
+ * tensor copies.  Any other A (pointers must still be aligned to the element
+ * size, else MISALIGNED) is staged column by column by bulk copies in regime
+ * (i), and in regime (ii) copied first into an aligned scratch buffer taken
+ * from the device's stream-ordered memory pool (cudaMallocAsync on `stream`,
+ * released by cudaFreeAsync after the kernel; if that allocation fails, a
+ * slower kernel with plain loads reads A directly).  Enqueues one to three
+ * kernels on `stream` and returns.
  */
 TSMM_API tsmm_status tsmm_execute(tsmm_plan_t plan, double alpha, const void *A_dev, int64_t lda,
                          tsmm_packed_b pb, double beta, void *C_dev, int64_t ldc,
@@ -219,7 +223,9 @@ TSMM_API tsmm_status tsmm_execute(tsmm_plan_t plan, double alpha, const void *A_
  */
 TSMM_API tsmm_status tsmm_plan_check(tsmm_plan_t plan);
 
-/* Number of kernel launches `tsmm_execute` with this plan enqueues (for accounting). */
+/* Number of kernel launches `tsmm_execute` with this plan enqueues for an A that
+ * a tensor map can describe (for accounting; regime (ii) with any other A adds
+ * the copy kernel). */
 TSMM_API int tsmm_plan_launches_per_execute(tsmm_plan_t plan);
 
 /*

@@ -510,15 +510,58 @@ tsmm_status tsmm_execute(tsmm_plan_t p, double alpha, const void *A_dev, int64_t
         ra.alpha = alpha;
         ra.beta = beta;
         ra.num_sms = p->num_sms;
+        // An A that a tensor map cannot describe is small here (k <= 128 columns
+        // against an m x n output): it is copied into an aligned scratch buffer
+        // from the stream's memory pool (released on the stream after the
+        // kernel) so that the tensor-copy kernels run; only if that allocation
+        // fails does the plain-load kernel read it directly.
+        void *scratch = nullptr;
+        CUtensorMap tm_scratch;
+        bool tma_a = tma;
+        if (!tma && encoder() != nullptr && m < INT_MAX && k <= 65535) {
+            const int64_t v = 16 / (int64_t)es;
+            const int64_t ldd = (m + v - 1) / v * v;
+            const size_t bytes = (size_t)ldd * (size_t)k * es;
+            if (bytes <= (size_t(1) << 32) && cudaMallocAsync(&scratch, bytes, s) == cudaSuccess) {
+                const cuuint64_t gdim[2] = {(cuuint64_t)m, (cuuint64_t)k};
+                const cuuint64_t gstride[1] = {(cuuint64_t)(ldd * (int64_t)es)};
+                const cuuint32_t box[2] = {(cuuint32_t)p->bm,
+                                           (cuuint32_t)a_box_k(p->dtype, p->regime, p->precision, p->k)};
+                const cuuint32_t estr[2] = {1, 1};
+                const cudaError_t ce = launch_copy_columns(p->dtype, A_dev, lda, m, k, scratch, ldd, s);
+                if (ce == cudaSuccess &&
+                    encoder()(&tm_scratch,
+                              p->dtype == TSMM_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64,
+                              2, scratch, gdim, gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS) {
+                    tma_a = true;
+                    ra.A = scratch;
+                    ra.lda = ldd;
+                } else {
+                    cudaFreeAsync(scratch, s);
+                    scratch = nullptr;
+                    if (ce != cudaSuccess) return cuda_status(ce);
+                }
+            } else {
+                cudaGetLastError();  // no scratch: the plain-load kernel
+                scratch = nullptr;
+            }
+        }
         // C tiles by TMA (C0 prefetch; C0 and C in the FP32 k > 32 kernel): the
         // same 16-byte rules for C
-        const bool tmc = tma && c_tma_ok(C_dev, ldc, n, es);
+        const bool tmc = tma_a && c_tma_ok(C_dev, ldc, n, es);
         if (tmc) {
             const tsmm_status st = encode_tmapc(p, C_dev, m, n, ldc, es, kRankNT);
-            if (st != TSMM_OK) return st;
+            if (st != TSMM_OK) {
+                if (scratch) cudaFreeAsync(scratch, s);
+                return st;
+            }
         }
-        return cuda_status(launch_rankk(p->dtype, tma ? &p->tmap : nullptr, tmc ? &p->tmapc : nullptr,
-                                        ra, p->status, s));
+        const cudaError_t e = launch_rankk(p->dtype, tma_a ? (scratch ? &tm_scratch : &p->tmap) : nullptr,
+                                           tmc ? &p->tmapc : nullptr, ra, p->status, s);
+        if (scratch) cudaFreeAsync(scratch, s);  // after the kernel, in stream order
+        return cuda_status(e);
     }
     cudaError_t e = p->dtype == TSMM_F32 ? launch_tall_f32(tma, p->np, &p->tmap, a, s)
                                          : launch_tall_f64(tma, p->np, &p->tmap, a, s);

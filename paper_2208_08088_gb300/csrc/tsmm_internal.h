@@ -231,5 +231,7 @@ cudaError_t launch_pack_b(tsmm_dtype dt, int64_t k, int64_t n, const void *B, in
                           void *dst, int64_t kp, int64_t w, int64_t ntiles, cudaStream_t s);
 cudaError_t launch_scale(tsmm_dtype dt, int64_t m, int64_t n, double beta, void *C, int64_t ldc,
                          cudaStream_t s);
+cudaError_t launch_copy_columns(tsmm_dtype dt, const void *src, int64_t lds, int64_t m, int64_t k, void *dst,
+                                int64_t ldd, cudaStream_t s);
 
 }  // namespace tsmm

@@ -35,6 +35,18 @@ __global__ void scale_kernel(int64_t m, int64_t n, T beta, T *__restrict__ C, in
     }
 }
 
+// dst[i + p*ldd] = src[i + p*lds] for i < m, p < k (blockIdx.y = p): a
+// column-major copy into another leading dimension.  Regime (ii) uses it to give
+// an A that a tensor map cannot describe an aligned copy that one can.
+template <typename T>
+__global__ void copy_columns_kernel(const T *__restrict__ src, int64_t lds, int64_t m, T *__restrict__ dst,
+                                    int64_t ldd) {
+    const T *sc = src + (int64_t)blockIdx.y * lds;
+    T *dc = dst + (int64_t)blockIdx.y * ldd;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x)
+        dc[i] = sc[i];
+}
+
 static unsigned grid_for(int64_t total, int threads) {
     int64_t blocks = (total + threads - 1) / threads;
     if (blocks > 152 * 64) blocks = 152 * 64;
@@ -53,6 +65,23 @@ cudaError_t launch_pack_b(tsmm_dtype dt, int64_t k, int64_t n, const void *B, in
     else
         pack_b_kernel<double><<<grid_for(total, threads), threads, 0, s>>>(
             static_cast<const double *>(B), k, n, ldb, static_cast<double *>(dst), kp, w, total);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_copy_columns(tsmm_dtype dt, const void *src, int64_t lds, int64_t m, int64_t k, void *dst,
+                                int64_t ldd, cudaStream_t s) {
+    if (m == 0 || k == 0) return cudaSuccess;
+    if (k > 65535) return cudaErrorInvalidValue;
+    const int threads = 256;
+    int64_t bx = (m + threads - 1) / threads;
+    if (bx > 64) bx = 64;
+    const dim3 grid((unsigned)bx, (unsigned)k);
+    if (dt == TSMM_F32)
+        copy_columns_kernel<float><<<grid, threads, 0, s>>>(static_cast<const float *>(src), lds, m,
+                                                            static_cast<float *>(dst), ldd);
+    else
+        copy_columns_kernel<double><<<grid, threads, 0, s>>>(static_cast<const double *>(src), lds, m,
+                                                             static_cast<double *>(dst), ldd);
     return cudaGetLastError();
 }
 

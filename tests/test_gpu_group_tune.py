@@ -173,6 +173,12 @@ def test_cuda_graph_replay_matches_eager():
         pb = tsmm.pack_b(dB)
         dC = to_device(np.zeros((m, n), dtype=np.float32, order="F"))
         ops.append((pl, dA, pb, dC, A, B))
+    # regime (ii) with an A that a tensor map cannot describe: its scratch copy is
+    # allocated and freed on the stream (memory nodes of the graph)
+    m, n, k = 3001, 200, 40
+    A, B, C0, _, dB = problem(m, n, k, np.float32, 340)
+    ops.append((tsmm.plan(m, n, k, torch.float32), to_device(A, ld=m), tsmm.pack_b(dB),
+                to_device(np.zeros((m, n), dtype=np.float32, order="F")), A, B))
     s = torch.cuda.Stream()
     s.wait_stream(torch.cuda.current_stream())
     with torch.cuda.stream(s):

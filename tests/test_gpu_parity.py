@@ -218,6 +218,24 @@ def test_rankk_integer_exact_and_padded(dtype):
     assert np.array_equal(C, C2)
 
 
+@pytest.mark.parametrize("dtype", DT)
+@pytest.mark.parametrize("k", [4, 16, 32, 64, 128])
+def test_rankk_unaligned_A_equals_aligned(dtype, k):
+    """An A that a tensor map cannot describe (lda*s or the base not a multiple
+    of 16 bytes) is copied into an aligned scratch buffer on the stream, so
+    regime (ii) then runs the same kernels: bit for bit the aligned result, with
+    C aligned (TMA epilogue) and not (plain epilogue)."""
+    m, n = 1001, 700
+    A, B, C0 = gen(m, n, k, dtype)
+    pl = pb = None
+    for ldc in (1004, 1001):  # C described by a tensor map, and not
+        ref, pl, pb = run(A, B, C0, 1.25, 0.75, lda=1004, ldc=ldc, plan=pl, pb=pb)
+        for lda, off in ((1001, 0), (1003, 2), (1004, 1)):
+            C, _, _ = run(A, B, C0, 1.25, 0.75, lda=lda, ldc=ldc, a_offset=off, plan=pl, pb=pb)
+            assert np.array_equal(C, ref), f"lda={lda} offset={off} ldc={ldc}"
+        assert_parity(ref, A, B, C0, 1.25, 0.75)
+
+
 # ------------------------------------------------------------- packing + ABI errors
 @pytest.mark.parametrize("dtype", DT)
 @pytest.mark.parametrize("k,n", [(1, 1), (33, 5), (100, 64), (7, 65), (128, 300)])

@@ -16,8 +16,10 @@
 // STAGES mbarrier-guarded buffers.  For the output-bound small-k shapes
 // (PREFETCH_C0) it also fetches the whole C0 tile with one tensor copy at block
 // start, so the C0 read overlaps the A/B traffic and the products; otherwise
-// the epilogue loads C0 in batches ahead of its stores.  A plain-load kernel
-// covers unaligned A.
+// the epilogue loads C0 in batches ahead of its stores.  An A that a tensor
+// map cannot describe is first copied into an aligned scratch buffer by the
+// host-side dispatch (tsmm_execute); the plain-load kernel below covers it only
+// when no scratch can be had.
 #include <type_traits>
 
 #include "tsmm_device.cuh"

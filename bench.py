@@ -317,13 +317,23 @@ KERNEL_SOURCES = {  # the files that define each kernel family's device code
 }
 
 
+def code_text(source):
+    """C++/CUDA source without its comments and with whitespace collapsed: what
+    the hash of a kernel family follows (its code, not its documentation)."""
+    import re
+
+    source = re.sub(r"/\*.*?\*/", " ", source, flags=re.S)
+    source = re.sub(r"//[^\n]*", " ", source)
+    return " ".join(source.split())
+
+
 def kernel_source_hash(family):
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2208_08088_gb300", "csrc")
     for name in KERNEL_SOURCES[family]:
-        with open(os.path.join(csrc, name), "rb") as f:
+        with open(os.path.join(csrc, name), encoding="utf-8") as f:
             h.update(name.encode())
-            h.update(f.read())
+            h.update(code_text(f.read()).encode())
     return h.hexdigest()[:16]
 
 

@@ -79,3 +79,17 @@ def test_serving_stall_metric():
     held = [{"arrival_s": 0.0, "complete_s": 0.001}, {"arrival_s": 0.0, "complete_s": 0.2}]
     assert abs(bench.longest_stall_ms(held) - 199.0) < 1e-6
     assert bench.longest_stall_ms(held[:1]) == 0.0
+
+
+def test_kernel_source_hash_follows_code_not_comments():
+    """The traffic records are tied to a kernel family's code: comments and
+    whitespace do not change code_text, a changed token does."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    a = "int x = 1; // one\n/* block\n comment */ int y = x +  2;\n"
+    b = "int x = 1;   // other words\nint y = x + 2; /* c */\n"
+    c = "int x = 1;\nint y = x + 3;\n"
+    assert bench.code_text(a) == bench.code_text(b) == "int x = 1; int y = x + 2;"
+    assert bench.code_text(c) != bench.code_text(a)
+    assert len(bench.kernel_source_hash("tall")) == 16

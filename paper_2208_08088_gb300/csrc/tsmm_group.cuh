@@ -71,30 +71,43 @@ cudaError_t launch_grouped_t(const GroupParams &gp, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// Per-width dispatch of the grouped kernel: tensor-map A (tsmm_group_<dtype>.cu)
+// and, in its load form lv, an A that a tensor map cannot describe
+// (tsmm_group_async_<dtype>.cu), in translation units of their own.
+template <typename T>
+cudaError_t launch_grouped_tma_dispatch(int np, const GroupParams &gp, cudaStream_t s) {
+#define TSMM_GROUP_CASE(NPV) \
+    case NPV:                \
+        return launch_grouped_t<T, NPV, false, -1>(gp, s);
+    switch (np) {
+        TSMM_FOR_TALL_WIDTHS(TSMM_GROUP_CASE)
+        default:
+            return cudaErrorInvalidValue;
+    }
+#undef TSMM_GROUP_CASE
+}
+
 template <typename T, int NP>
-cudaError_t launch_grouped_np(bool unaligned, int lv, const GroupParams &gp, cudaStream_t s) {
-    if (!unaligned) return launch_grouped_t<T, NP, false, -1>(gp, s);
+cudaError_t launch_grouped_async_np(int lv, const GroupParams &gp, cudaStream_t s) {
     return with_load_variant<T, NP>(lv, [&](auto lv_tag) {
         return launch_grouped_t<T, NP, true, decltype(lv_tag)::value>(gp, s);
     });
 }
 
-// unaligned: problems whose A a tensor map cannot describe (the U kernel, in
-// load form lv)
 template <typename T>
-cudaError_t launch_grouped_dispatch(int np, bool unaligned, int lv, const GroupParams &gp, cudaStream_t s) {
+cudaError_t launch_grouped_async_dispatch(int np, int lv, const GroupParams &gp, cudaStream_t s) {
+#define TSMM_GROUP_CASE(NPV) \
+    case NPV:                \
+        return launch_grouped_async_np<T, NPV>(lv, gp, s);
     switch (np) {
-        case 1: return launch_grouped_np<T, 1>(unaligned, lv, gp, s);
-        case 2: return launch_grouped_np<T, 2>(unaligned, lv, gp, s);
-        case 4: return launch_grouped_np<T, 4>(unaligned, lv, gp, s);
-        case 8: return launch_grouped_np<T, 8>(unaligned, lv, gp, s);
-        case 16: return launch_grouped_np<T, 16>(unaligned, lv, gp, s);
-        case 24: return launch_grouped_np<T, 24>(unaligned, lv, gp, s);
-        case 32: return launch_grouped_np<T, 32>(unaligned, lv, gp, s);
-        case 48: return launch_grouped_np<T, 48>(unaligned, lv, gp, s);
-        case 64: return launch_grouped_np<T, 64>(unaligned, lv, gp, s);
-        default: return cudaErrorInvalidValue;
+        TSMM_FOR_TALL_WIDTHS(TSMM_GROUP_CASE)
+        default:
+            return cudaErrorInvalidValue;
     }
+#undef TSMM_GROUP_CASE
 }
+
+cudaError_t launch_grouped_async_f32(int np, int lv, const GroupParams &gp, cudaStream_t s);
+cudaError_t launch_grouped_async_f64(int np, int lv, const GroupParams &gp, cudaStream_t s);
 
 }  // namespace tsmm

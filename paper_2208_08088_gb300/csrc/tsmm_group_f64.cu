@@ -1,8 +1,9 @@
-// FP64 instantiations of the grouped regime (i) kernel.
+// FP64 instantiations of the grouped regime (i) kernel for tensor-map A (an A
+// that a tensor map cannot describe: tsmm_group_async_f64.cu).
 #include "tsmm_group.cuh"
 
 namespace tsmm {
 cudaError_t launch_grouped_f64(int np, bool unaligned, int lv, const GroupParams &gp, cudaStream_t s) {
-    return launch_grouped_dispatch<double>(np, unaligned, lv, gp, s);
+    return unaligned ? launch_grouped_async_f64(np, lv, gp, s) : launch_grouped_tma_dispatch<double>(np, gp, s);
 }
 }  // namespace tsmm

@@ -685,27 +685,39 @@ cudaError_t launch_tall_async_t(const TallArgs &a, cudaStream_t s) {
     });
 }
 
+// Per-width dispatch of the two regime (i) kernels.  Each dtype's TMA and
+// bulk-copy kernels are instantiated in translation units of their own
+// (tsmm_tall_<dtype>.cu, tsmm_tall_async_<dtype>.cu) so that they compile in
+// parallel.
+#define TSMM_FOR_TALL_WIDTHS(X) X(1) X(2) X(4) X(8) X(16) X(24) X(32) X(48) X(64)
+
 template <typename T>
-cudaError_t launch_tall_dispatch(bool tma, int np, const CUtensorMap *tmap, const TallArgs &a,
-                                 cudaStream_t s) {
-#define TSMM_TALL_CASE(NPV)                                                       \
-    case NPV:                                                                     \
-        return tma ? launch_tall_tma_t<T, NPV>(tmap, a, s)                        \
-                   : launch_tall_async_t<T, NPV>(a, s);
+cudaError_t launch_tall_tma_dispatch(int np, const CUtensorMap *tmap, const TallArgs &a, cudaStream_t s) {
+#define TSMM_TALL_CASE(NPV) \
+    case NPV:               \
+        return launch_tall_tma_t<T, NPV>(tmap, a, s);
     switch (np) {
-        TSMM_TALL_CASE(1)
-        TSMM_TALL_CASE(2)
-        TSMM_TALL_CASE(4)
-        TSMM_TALL_CASE(8)
-        TSMM_TALL_CASE(16)
-        TSMM_TALL_CASE(24)
-        TSMM_TALL_CASE(32)
-        TSMM_TALL_CASE(48)
-        TSMM_TALL_CASE(64)
+        TSMM_FOR_TALL_WIDTHS(TSMM_TALL_CASE)
         default:
             return cudaErrorInvalidValue;
     }
 #undef TSMM_TALL_CASE
 }
+
+template <typename T>
+cudaError_t launch_tall_async_dispatch(int np, const TallArgs &a, cudaStream_t s) {
+#define TSMM_TALL_CASE(NPV) \
+    case NPV:               \
+        return launch_tall_async_t<T, NPV>(a, s);
+    switch (np) {
+        TSMM_FOR_TALL_WIDTHS(TSMM_TALL_CASE)
+        default:
+            return cudaErrorInvalidValue;
+    }
+#undef TSMM_TALL_CASE
+}
+
+cudaError_t launch_tall_async_f32(int np, const TallArgs &a, cudaStream_t s);  // tsmm_tall_async_f32.cu
+cudaError_t launch_tall_async_f64(int np, const TallArgs &a, cudaStream_t s);  // tsmm_tall_async_f64.cu
 
 }  // namespace tsmm

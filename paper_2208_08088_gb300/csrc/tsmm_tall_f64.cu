@@ -1,9 +1,10 @@
-// FP64 instantiations of the regime (i) kernels.
+// FP64 instantiations of the regime (i) TMA kernel (the bulk-copy kernel for
+// an A that a tensor map cannot describe: tsmm_tall_async_f64.cu).
 #include "tsmm_tall.cuh"
 
 namespace tsmm {
 cudaError_t launch_tall_f64(bool tma, int np, const CUtensorMap *tmap, const TallArgs &a,
                             cudaStream_t s) {
-    return launch_tall_dispatch<double>(tma, np, tmap, a, s);
+    return tma ? launch_tall_tma_dispatch<double>(np, tmap, a, s) : launch_tall_async_f64(np, a, s);
 }
 }  // namespace tsmm

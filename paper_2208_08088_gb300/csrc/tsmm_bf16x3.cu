@@ -885,12 +885,22 @@ __global__ void __launch_bounds__(512, 1)
                             tma_load_2d(slot, &tmC, (int32_t)(mt * kBM), (int32_t)col0, &c_full[st], pol_c);
                         }
                     } else {
-                        // element e of the slot is (row e % 128, column e / 128)
-                        for (int e = lane; e < kBM * kRSUB; e += 32) {
-                            const int64_t row = mt * kBM + (e & (kBM - 1));
-                            const int64_t col = col0 + e / kBM;
-                            const bool in = row < a.m && col < a.n;
-                            cp_async_elem(slot + e, in ? C + row + col * a.ldc : C, in, 4);
+                        // element (row r, column c) of the slot sits at r + c * kBM; this
+                        // lane copies rows lane + 32 rr of every column, walking one
+                        // column pointer by ldc (a warp copy is one 128-byte run of C)
+                        const int64_t i0 = mt * kBM;
+                        bool rin[kBM / 32];
+#pragma unroll
+                        for (int rr = 0; rr < kBM / 32; ++rr) rin[rr] = i0 + lane + 32 * rr < a.m;
+                        const float *colp = C + i0 + lane + col0 * a.ldc;
+                        float *dst = slot + lane;
+                        for (int c = 0; c < kRSUB; ++c, colp += a.ldc, dst += kBM) {
+                            const bool cin = col0 + c < a.n;
+#pragma unroll
+                            for (int rr = 0; rr < kBM / 32; ++rr) {
+                                const bool in = cin && rin[rr];
+                                cp_async_elem(dst + 32 * rr, in ? colp + 32 * rr : C, in, 4);
+                            }
                         }
                         cp_async_arrive_noinc(&c_full[st]);
                     }

@@ -132,17 +132,73 @@ struct RankAcc<float> {
 // thread's C0 values -- from the tile sC ([BNT][BMT], as the tensor copy lays it
 // out) when given, else from global memory, all loads ahead of any store so
 // they do not wait behind stores to the same array; phase 2 stores.
+// The 16 bytes of consecutive elements at p, where p sits D elements past a
+// 16-byte boundary (D known at compile time): one 16-byte access for D = 0,
+// else the widest aligned pieces -- for FP32 two 8-byte accesses (D = 2) or
+// 4 + 8 + 4 bytes (D odd), for FP64 two 8-byte accesses.
+template <typename T, int D>
+__device__ __forceinline__ Vec<T, 16 / sizeof(T)> ld_group(const T *p) {
+    constexpr int V = 16 / (int)sizeof(T);
+    Vec<T, V> v;
+    if constexpr (D == 0) {
+        v = ld_vec<T, V>(p);
+    } else if constexpr (sizeof(T) == 4 && D == 2) {
+        const float2 q0 = *reinterpret_cast<const float2 *>(p);
+        const float2 q1 = *reinterpret_cast<const float2 *>(p + 2);
+        v.v[0] = q0.x, v.v[1] = q0.y, v.v[2] = q1.x, v.v[3] = q1.y;
+    } else if constexpr (sizeof(T) == 4) {
+        const float2 q = *reinterpret_cast<const float2 *>(p + 1);
+        v.v[0] = p[0], v.v[1] = q.x, v.v[2] = q.y, v.v[3] = p[3];
+    } else {
+#pragma unroll
+        for (int r = 0; r < V; ++r) v.v[r] = p[r];
+    }
+    return v;
+}
+template <typename T, int D>
+__device__ __forceinline__ void st_group(T *p, const Vec<T, 16 / sizeof(T)> &v) {
+    constexpr int V = 16 / (int)sizeof(T);
+    if constexpr (D == 0) {
+        st_vec<T, V>(p, v);
+    } else if constexpr (sizeof(T) == 4 && D == 2) {
+        *reinterpret_cast<float2 *>(p) = make_float2(v.v[0], v.v[1]);
+        *reinterpret_cast<float2 *>(p + 2) = make_float2(v.v[2], v.v[3]);
+    } else if constexpr (sizeof(T) == 4) {
+        p[0] = v.v[0];
+        *reinterpret_cast<float2 *>(p + 1) = make_float2(v.v[1], v.v[2]);
+        p[3] = v.v[3];
+    } else {
+#pragma unroll
+        for (int r = 0; r < V; ++r) p[r] = v.v[r];
+    }
+}
+
+// f(std::integral_constant<int, I>{}) for I = B .. E-1, unrolled at compile time.
+template <int B, int E, typename F>
+__device__ __forceinline__ void rank_static_for(F &&f) {
+    if constexpr (B < E) {
+        f(std::integral_constant<int, B>{});
+        rank_static_for<B + 1, E>(f);
+    }
+}
+
+// Epilogue of the 8 x 4-tile kernels.  LVC (the form of C's accesses): -1 for
+// any C (element accesses), else C's base is 16-byte aligned and ldc = LVC mod
+// V, so the thread's group of V rows in column c (c = column mod 4, the same
+// for the whole warp) sits (c * LVC) mod V elements past a 16-byte boundary and
+// is read and written with ld_group / st_group.  LVC = 0 is the aligned case.
 template <typename T>
 struct RankEpilogue {
     using Cfg = RankCfg<T>;
     static constexpr int V = Cfg::VEC;
     Vec<T, V> c0v[4][2];
 
+    template <int LVC>
     __device__ __forceinline__ void load(const RankArgs &a, int64_t i0, int64_t tile, int tm, int tn,
-                                         bool vec_c, const T *sC, T beta) {
+                                         const T *sC, T beta) {
         const T *C = static_cast<const T *>(a.C);
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
+        rank_static_for<0, 4>([&](auto c_tag) {
+            constexpr int c = decltype(c_tag)::value;
             const int jl = tn * 4 + c;
             const int64_t j = tile * Cfg::BNT + jl;
 #pragma unroll
@@ -154,37 +210,36 @@ struct RankEpilogue {
                 if (beta == T(0) || j >= a.n) continue;
                 if (sC) {
                     c0v[c][rg] = ld_vec<T, V>(sC + jl * Cfg::BMT + il);
-                } else if (vec_c && i + V <= a.m) {
-                    c0v[c][rg] = ld_vec<T, V>(C + i + j * a.ldc);
+                } else if (LVC >= 0 && i + V <= a.m) {
+                    c0v[c][rg] = ld_group<T, LVC >= 0 ? (c * LVC) % V : 0>(C + i + j * a.ldc);
                 } else {
 #pragma unroll
                     for (int r = 0; r < V; ++r)
                         if (i + r < a.m) c0v[c][rg].v[r] = C[i + r + j * a.ldc];
                 }
             }
-        }
+        });
     }
 
     // alpha == 1 is a separate code path (the test is uniform), so the
     // epilogue issues no multiply by 1 and no per-element select: at small k
     // in FP64 the epilogue's arithmetic shares the FP64 pipe with the k
     // products of each output.
+    template <int LVC>
     __device__ __forceinline__ void store(const RankAcc<T> &acc, const RankArgs &a, int64_t i0,
-                                          int64_t tile, int tm, int tn, bool vec_c, T alpha,
-                                          T beta) const {
-        if (alpha == T(1)) store_t<true>(acc, a, i0, tile, tm, tn, vec_c, alpha, beta);
-        else store_t<false>(acc, a, i0, tile, tm, tn, vec_c, alpha, beta);
+                                          int64_t tile, int tm, int tn, T alpha, T beta) const {
+        if (alpha == T(1)) store_t<true, LVC>(acc, a, i0, tile, tm, tn, alpha, beta);
+        else store_t<false, LVC>(acc, a, i0, tile, tm, tn, alpha, beta);
     }
 
-    template <bool ALPHA1>
+    template <bool ALPHA1, int LVC>
     __device__ __forceinline__ void store_t(const RankAcc<T> &acc, const RankArgs &a, int64_t i0,
-                                            int64_t tile, int tm, int tn, bool vec_c, T alpha,
-                                            T beta) const {
+                                            int64_t tile, int tm, int tn, T alpha, T beta) const {
         T *C = static_cast<T *>(a.C);
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
+        rank_static_for<0, 4>([&](auto c_tag) {
+            constexpr int c = decltype(c_tag)::value;
             const int64_t j = tile * Cfg::BNT + tn * 4 + c;
-            if (j >= a.n) continue;
+            if (j >= a.n) return;
 #pragma unroll
             for (int rg = 0; rg < 2; ++rg) {
                 const int64_t i = i0 + rg * (Cfg::BMT / 2) + tm * V;
@@ -196,15 +251,15 @@ struct RankEpilogue {
                     if (beta != T(0)) o.v[r] = fma(beta, c0v[c][rg].v[r], o.v[r]);
                 }
                 T *cp = C + i + j * a.ldc;
-                if (vec_c && i + V <= a.m) {
-                    st_vec<T, V>(cp, o);
+                if (LVC >= 0 && i + V <= a.m) {
+                    st_group<T, LVC >= 0 ? (c * LVC) % V : 0>(cp, o);
                 } else {
 #pragma unroll
                     for (int r = 0; r < V; ++r)
                         if (i + r < a.m) cp[r] = o.v[r];
                 }
             }
-        }
+        });
     }
 };
 
@@ -225,11 +280,10 @@ struct RankTmaCfg {
 // producer warp runs ahead of the consumers by up to STAGES k-chunks and, with
 // PREFETCH_C0, by one C0 tile, so the next tile's loads overlap this tile's
 // products and stores.
-template <typename T, int STAGES, bool PREFETCH_C0, bool C0_INIT = false>
+template <typename T, int STAGES, bool PREFETCH_C0, bool C0_INIT, int LVC>
 __global__ void __launch_bounds__(RankCfg<T>::CONSUMERS + 32, 2)
     rankk_tma_kernel(const __grid_constant__ CUtensorMap tmA,
-                     const __grid_constant__ CUtensorMap tmC, const RankArgs a, bool vec_c,
-                     unsigned *status) {
+                     const __grid_constant__ CUtensorMap tmC, const RankArgs a, unsigned *status) {
     using Cfg = RankCfg<T>;
     using TC = RankTmaCfg<T, STAGES, PREFETCH_C0>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -331,7 +385,7 @@ __global__ void __launch_bounds__(RankCfg<T>::CONSUMERS + 32, 2)
                 return;  // this warp's part of the tile is not written; the host sees TSMM_ERR_TIMEOUT
             }
             RankEpilogue<T> e0;
-            e0.load(a, i0, tile, tm, tn, vec_c, sC + b * Cfg::C_TILE, ebeta);
+            e0.template load<LVC>(a, i0, tile, tm, tn, sC + b * Cfg::C_TILE, ebeta);
             release_reads_to_async_copy();
             __syncwarp();
             if (lane == 0) mbar_arrive(&cempty[b]);  // C0 buffer b may be refilled
@@ -358,7 +412,7 @@ __global__ void __launch_bounds__(RankCfg<T>::CONSUMERS + 32, 2)
                 if (lane == 0) atomicOr(status, kDevErrTimeout);
                 return;
             }
-            RankEpilogue<T>().store(acc, a, i0, tile, tm, tn, vec_c, T(1), T(0));  // C0 is in acc
+            RankEpilogue<T>().template store<LVC>(acc, a, i0, tile, tm, tn, T(1), T(0));  // C0 is in acc
             continue;
         }
         RankEpilogue<T> ep;
@@ -368,19 +422,19 @@ __global__ void __launch_bounds__(RankCfg<T>::CONSUMERS + 32, 2)
             if (lane == 0) atomicOr(status, kDevErrTimeout);
             return;  // this warp's part of the tile is not written; the host sees TSMM_ERR_TIMEOUT
         }
-        ep.load(a, i0, tile, tm, tn, vec_c, want_c0 ? sC + b * Cfg::C_TILE : nullptr, ebeta);
+        ep.template load<LVC>(a, i0, tile, tm, tn, want_c0 ? sC + b * Cfg::C_TILE : nullptr, ebeta);
         if (want_c0) {
             release_reads_to_async_copy();
             __syncwarp();
             if (lane == 0) mbar_arrive(&cempty[b]);  // C0 buffer b may be refilled
         }
-        ep.store(acc, a, i0, tile, tm, tn, vec_c, ealpha, ebeta);
+        ep.template store<LVC>(acc, a, i0, tile, tm, tn, ealpha, ebeta);
     }
 }
 
 // Plain-load kernel for an A that a tensor map cannot describe.
-template <typename T>
-__global__ void __launch_bounds__(256, 2) rankk_plain_kernel(const RankArgs a, bool vec_a, bool vec_c) {
+template <typename T, int LVC>
+__global__ void __launch_bounds__(256, 2) rankk_plain_kernel(const RankArgs a, bool vec_a) {
     using Cfg = RankCfg<T>;
     constexpr int V = Cfg::VEC;
     constexpr int BMT = Cfg::BMT;
@@ -436,8 +490,8 @@ __global__ void __launch_bounds__(256, 2) rankk_plain_kernel(const RankArgs a, b
         __syncthreads();
     }
     RankEpilogue<T> ep;
-    ep.load(a, i0, tile, tm, tn, vec_c, nullptr, ebeta);
-    ep.store(acc, a, i0, tile, tm, tn, vec_c, ealpha, ebeta);
+    ep.template load<LVC>(a, i0, tile, tm, tn, nullptr, ebeta);
+    ep.template store<LVC>(acc, a, i0, tile, tm, tn, ealpha, ebeta);
 }
 
 // FP32, k > 32 (FMA-bound).  A 16-byte shared-memory load costs
@@ -554,10 +608,10 @@ __device__ __forceinline__ void tma_store_2d_commit(const void *tmap, const void
 }
 }  // namespace
 
-template <bool TMA_EPI, int KC>
+template <bool TMA_EPI, int KC, int LVC>
 __global__ void __launch_bounds__(WideCfg<TMA_EPI, KC>::THREADS, WideCfg<TMA_EPI, KC>::RESIDENT)
     rankk_wide_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmC,
-                      const RankArgs a, bool vec_c, unsigned *status) {
+                      const RankArgs a, unsigned *status) {
     using W = WideCfg<TMA_EPI, KC>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float *sStage = reinterpret_cast<float *>(smem_raw);
@@ -705,41 +759,47 @@ __global__ void __launch_bounds__(WideCfg<TMA_EPI, KC>::THREADS, WideCfg<TMA_EPI
             __syncwarp();
             if (lane == 0) mbar_arrive(cstore);
         } else {
-            // plain epilogue in two halves of 4 columns: all C0 loads of a half before its stores
+            // plain epilogue in two halves of 4 columns: all C0 loads of a half before its
+            // stores; column cc of a half is cc mod 4 of the tile, so with LVC >= 0 its rows
+            // sit (cc * LVC) mod 4 elements past a 16-byte boundary (RankEpilogue's forms)
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
-                float4 c0v[4][2];
-#pragma unroll
-                for (int cc = 0; cc < 4; ++cc) {
+                Vec<float, 4> c0v[4][2];
+                rank_static_for<0, 4>([&](auto cc_tag) {
+                    constexpr int cc = decltype(cc_tag)::value;
                     const int64_t jg = tile * W::BNT + c0 + h * 16 + cc;
 #pragma unroll
                     for (int rg = 0; rg < 2; ++rg) {
                         const int64_t i = i0 + r0 + rg * 32;
-                        c0v[cc][rg] = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                        for (int r = 0; r < 4; ++r) c0v[cc][rg].v[r] = 0.f;
                         if (!use_c0 || jg >= a.n) continue;
                         const float *src = C + i + jg * a.ldc;
-                        if (vec_c && i + 4 <= a.m) {
-                            c0v[cc][rg] = *reinterpret_cast<const float4 *>(src);
+                        if (LVC >= 0 && i + 4 <= a.m) {
+                            c0v[cc][rg] = ld_group<float, LVC >= 0 ? (cc * LVC) % 4 : 0>(src);
                         } else {
-                            if (i < a.m) c0v[cc][rg].x = src[0];
-                            if (i + 1 < a.m) c0v[cc][rg].y = src[1];
-                            if (i + 2 < a.m) c0v[cc][rg].z = src[2];
-                            if (i + 3 < a.m) c0v[cc][rg].w = src[3];
+#pragma unroll
+                            for (int r = 0; r < 4; ++r)
+                                if (i + r < a.m) c0v[cc][rg].v[r] = src[r];
                         }
                     }
-                }
-#pragma unroll
-                for (int cc = 0; cc < 4; ++cc) {
+                });
+                rank_static_for<0, 4>([&](auto cc_tag) {
+                    constexpr int cc = decltype(cc_tag)::value;
                     const int64_t jg = tile * W::BNT + c0 + h * 16 + cc;
-                    if (jg >= a.n) continue;
+                    if (jg >= a.n) return;
 #pragma unroll
                     for (int rg = 0; rg < 2; ++rg) {
                         const int64_t i = i0 + r0 + rg * 32;
                         const float4 x = acc.rows(rg, h * 4 + cc);
-                        const float4 o = axpby4(alpha, x, beta, c0v[cc][rg], use_c0);
+                        const Vec<float, 4> &cv = c0v[cc][rg];
+                        const float4 o =
+                            axpby4(alpha, x, beta, make_float4(cv.v[0], cv.v[1], cv.v[2], cv.v[3]), use_c0);
                         float *dst = C + i + jg * a.ldc;
-                        if (vec_c && i + 4 <= a.m) {
-                            *reinterpret_cast<float4 *>(dst) = o;
+                        if (LVC >= 0 && i + 4 <= a.m) {
+                            Vec<float, 4> ov;
+                            ov.v[0] = o.x, ov.v[1] = o.y, ov.v[2] = o.z, ov.v[3] = o.w;
+                            st_group<float, LVC >= 0 ? (cc * LVC) % 4 : 0>(dst, ov);
                         } else {
                             if (i < a.m) dst[0] = o.x;
                             if (i + 1 < a.m) dst[1] = o.y;
@@ -747,45 +807,65 @@ __global__ void __launch_bounds__(WideCfg<TMA_EPI, KC>::THREADS, WideCfg<TMA_EPI
                             if (i + 3 < a.m) dst[3] = o.w;
                         }
                     }
-                }
+                });
             }
         }
     }
     if (!ok && lane == 0) atomicOr(status, kDevErrTimeout);
 }
 
-template <bool TMA_EPI, int KC>
+template <bool TMA_EPI, int KC, int LVC>
 static cudaError_t launch_rankk_wide_t(const CUtensorMap *tmA, const CUtensorMap *tmC, const RankArgs &a,
-                                       bool vec_c, unsigned *status, cudaStream_t s) {
+                                       unsigned *status, cudaStream_t s) {
     using W = WideCfg<TMA_EPI, KC>;
     {
         const cudaError_t e =
-            ensure_smem_limit(reinterpret_cast<const void *>(rankk_wide_kernel<TMA_EPI, KC>), W::SMEM);
+            ensure_smem_limit(reinterpret_cast<const void *>(rankk_wide_kernel<TMA_EPI, KC, LVC>), W::SMEM);
         if (e != cudaSuccess) return e;
     }
     const int64_t tiles = ((a.m + W::BMT - 1) / W::BMT) * ((a.n + W::BNT - 1) / W::BNT);
     const int64_t slots = W::RESIDENT * (int64_t)(a.num_sms > 0 ? a.num_sms : 1);
     const unsigned grid = (unsigned)(tiles < slots ? tiles : slots);
-    rankk_wide_kernel<TMA_EPI, KC><<<grid, W::THREADS, W::SMEM, s>>>(*tmA, *tmC, a, vec_c, status);
+    rankk_wide_kernel<TMA_EPI, KC, LVC><<<grid, W::THREADS, W::SMEM, s>>>(*tmA, *tmC, a, status);
     return cudaGetLastError();
 }
 
-template <typename T, int STAGES, bool PF, bool C0I = false>
+template <typename T, int STAGES, bool PF, bool C0I, int LVC>
 static cudaError_t launch_rankk_tma_t(const CUtensorMap *tmA, const CUtensorMap *tmC,
-                                      const RankArgs &a, bool vec_c, unsigned *status,
-                                      cudaStream_t s) {
+                                      const RankArgs &a, unsigned *status, cudaStream_t s) {
     using Cfg = RankCfg<T>;
     using TC = RankTmaCfg<T, STAGES, PF>;
     {
         const cudaError_t e = ensure_smem_limit(
-            reinterpret_cast<const void *>(rankk_tma_kernel<T, STAGES, PF, C0I>), TC::SMEM);
+            reinterpret_cast<const void *>(rankk_tma_kernel<T, STAGES, PF, C0I, LVC>), TC::SMEM);
         if (e != cudaSuccess) return e;
     }
     const int64_t tiles = ((a.m + Cfg::BMT - 1) / Cfg::BMT) * ((a.n + Cfg::BNT - 1) / Cfg::BNT);
     const int64_t slots = (int64_t)TC::RESIDENT * (a.num_sms > 0 ? a.num_sms : 1);
     const unsigned grid = (unsigned)(tiles < slots ? tiles : slots);
-    rankk_tma_kernel<T, STAGES, PF, C0I><<<grid, TC::THREADS, TC::SMEM, s>>>(*tmA, *tmC, a, vec_c, status);
+    rankk_tma_kernel<T, STAGES, PF, C0I, LVC><<<grid, TC::THREADS, TC::SMEM, s>>>(*tmA, *tmC, a, status);
     return cudaGetLastError();
+}
+
+// Calls f(std::integral_constant<int, LVC>) for the form lvc of C's accesses
+// (RankEpilogue): FP32 -1..3, FP64 -1..1.
+template <typename T, typename F>
+static cudaError_t with_c_form(int lvc, F &&f) {
+    switch (lvc) {
+        case 0:
+            return f(std::integral_constant<int, 0>{});
+        case 1:
+            return f(std::integral_constant<int, 1>{});
+        case 2:
+            if constexpr (sizeof(T) == 4) return f(std::integral_constant<int, 2>{});
+            break;
+        case 3:
+            if constexpr (sizeof(T) == 4) return f(std::integral_constant<int, 3>{});
+            break;
+        default:
+            break;
+    }
+    return f(std::integral_constant<int, -1>{});
 }
 
 template <typename T>
@@ -794,33 +874,43 @@ static cudaError_t launch_rankk_t(const CUtensorMap *tmA, const CUtensorMap *tmC
     using Cfg = RankCfg<T>;
     const bool vec_a = (reinterpret_cast<uintptr_t>(a.A) % 16 == 0) &&
                        ((a.lda * (int64_t)sizeof(T)) % 16 == 0);
-    const bool vec_c = (reinterpret_cast<uintptr_t>(a.C) % 16 == 0) &&
-                       ((a.ldc * (int64_t)sizeof(T)) % 16 == 0);
+    // form of C's accesses: ldc mod (16 bytes / element) for a 16-byte aligned base, else -1
+    const int lvc = reinterpret_cast<uintptr_t>(a.C) % 16 == 0 ? (int)((uint64_t)a.ldc % (16 / sizeof(T))) : -1;
     if (tmA) {
         // FP32 from k = kRankWideMinK on: the 8 x 8-tile kernel (its A tensor map's box is
-        // 128 x rank_wide_kc(k))
+        // 128 x rank_wide_kc(k)); C by TMA when its tensor map exists, else in form lvc
         if (rank_wide(sizeof(T) == 4 ? TSMM_F32 : TSMM_F64, 2, 0, a.k)) {
-            if (rank_wide_kc(a.k) == 16)
-                return tmC ? launch_rankk_wide_t<true, 16>(tmA, tmC, a, vec_c, status, s)
-                           : launch_rankk_wide_t<false, 16>(tmA, tmA, a, vec_c, status, s);
-            return tmC ? launch_rankk_wide_t<true, 32>(tmA, tmC, a, vec_c, status, s)
-                       : launch_rankk_wide_t<false, 32>(tmA, tmA, a, vec_c, status, s);
+            if (rank_wide_kc(a.k) == 16) {
+                if (tmC) return launch_rankk_wide_t<true, 16, 0>(tmA, tmC, a, status, s);
+                return with_c_form<T>(lvc, [&](auto f) {
+                    return launch_rankk_wide_t<false, 16, decltype(f)::value>(tmA, tmA, a, status, s);
+                });
+            }
+            if (tmC) return launch_rankk_wide_t<true, 32, 0>(tmA, tmC, a, status, s);
+            return with_c_form<T>(lvc, [&](auto f) {
+                return launch_rankk_wide_t<false, 32, decltype(f)::value>(tmA, tmA, a, status, s);
+            });
         }
         // output-bound shapes: one k chunk, C0 prefetched by TMA when it is read
         if (a.k <= Cfg::KC) {
             if (tmC && a.beta != 0.0) {
                 if constexpr (std::is_same<T, double>::value)
                     if (a.alpha == 1.0 && a.beta == 1.0)
-                        return launch_rankk_tma_t<T, 1, true, true>(tmA, tmC, a, vec_c, status, s);
-                return launch_rankk_tma_t<T, 1, true>(tmA, tmC, a, vec_c, status, s);
+                        return launch_rankk_tma_t<T, 1, true, true, 0>(tmA, tmC, a, status, s);
+                return launch_rankk_tma_t<T, 1, true, false, 0>(tmA, tmC, a, status, s);
             }
-            return launch_rankk_tma_t<T, 1, false>(tmA, tmA, a, vec_c, status, s);
+            return with_c_form<T>(lvc, [&](auto f) {
+                return launch_rankk_tma_t<T, 1, false, false, decltype(f)::value>(tmA, tmA, a, status, s);
+            });
         }
-        return launch_rankk_tma_t<T, 2, false>(tmA, tmA, a, vec_c, status, s);
+        return with_c_form<T>(lvc, [&](auto f) {
+            return launch_rankk_tma_t<T, 2, false, false, decltype(f)::value>(tmA, tmA, a, status, s);
+        });
     }
     const int smem = Cfg::KC * (Cfg::BMT + Cfg::BNT) * (int)sizeof(T);
     dim3 grid((unsigned)((a.m + Cfg::BMT - 1) / Cfg::BMT), (unsigned)((a.n + Cfg::BNT - 1) / Cfg::BNT));
-    rankk_plain_kernel<T><<<grid, Cfg::CONSUMERS, smem, s>>>(a, vec_a, vec_c);
+    if (lvc == 0) rankk_plain_kernel<T, 0><<<grid, Cfg::CONSUMERS, smem, s>>>(a, vec_a);
+    else rankk_plain_kernel<T, -1><<<grid, Cfg::CONSUMERS, smem, s>>>(a, vec_a);
     return cudaGetLastError();
 }
 

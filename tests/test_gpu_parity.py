@@ -306,12 +306,30 @@ def test_rankk_persistent_many_tiles(dtype, k, beta, m):
 
 @pytest.mark.parametrize("beta", [0.0, 1.0])
 @pytest.mark.parametrize("k", [33, 64, 128])
-@pytest.mark.parametrize("m,n", [(129, 65), (1000, 80), (1000, 96), (384, 97), (1000, 130), (2048, 1000)])
+@pytest.mark.parametrize("m,n", [(129, 65), (1000, 80), (1000, 96), (384, 97), (640, 70), (1000, 130),
+                                 (2048, 1000)])
 def test_rankk_tma_epilogue_edges_integer_exact(m, n, k, beta):
     """FP32 with k > 32 and C meeting the TMA rules (m = 129 does not: the plain
     epilogue) moves C0 and C as 128 x 64 tiles by tensor copies: ragged m and n
-    whose last tile is a quarter to seven eighths beyond n, beta = 0 over a
+    whose last tile is a quarter to seven eighths beyond m or n, beta = 0 over a
     NaN-filled C, integer inputs (exact)."""
+    A, B, C0 = gen(m, n, k, np.float32, "integer")
+    C, pl, _ = run(A, B, C0 if beta != 0 else None, 1.5, beta)
+    assert pl.info()["regime"] == 2
+    assert pl.info()["bm"] == 128
+    assert_parity(C, A, B, C0 if beta != 0 else None, 1.5, beta, exact=True)
+
+
+@pytest.mark.parametrize("beta", [0.0, 1.0])
+@pytest.mark.parametrize("k", [40, 100])
+@pytest.mark.parametrize("m", [2048, 2050])
+def test_rankk_wide_several_tiles_per_block(m, k, beta):
+    """FP32 with k > 32 over 1216 or more 128 x 64 tiles (n = 4864), so that
+    every one of the 2 x 152 persistent blocks walks four tiles or more through
+    its k-chunk ring and its C buffer (m = 2048: tensor copies for C0 and C;
+    m = 2050: plain loads and stores); k = 40 and 100 end in a partial chunk
+    of 32.  Integer inputs (exact)."""
+    n = 4864
     A, B, C0 = gen(m, n, k, np.float32, "integer")
     C, pl, _ = run(A, B, C0 if beta != 0 else None, 1.5, beta)
     assert pl.info()["regime"] == 2

@@ -169,10 +169,12 @@ TSMM_API tsmm_status tsmm_packed_b_read(tsmm_packed_b pb, void *host_dst, size_t
  * along n, Section IV.A.2), and allocates the split-K workspace and the
  * per-tile arrival counters on the current device.
  *
- * The plan is immutable once created and owns its workspace, so two
- * executions that may overlap on the device (different streams) need two
- * plans.  Errors: INVALID_ARG (negative sizes, bad dtype, NULL out),
- * UNSUPPORTED_SHAPE, OUT_OF_MEMORY, CUDA.
+ * The plan's shape and kernel choice are fixed once created; it owns its
+ * workspace and caches the tensor maps of the last A and C it ran with (each
+ * launch takes its own copy), so calls with one plan must come from one host
+ * thread at a time, and two executions that may overlap on the device
+ * (different streams) need two plans.  Errors: INVALID_ARG (negative sizes,
+ * bad dtype, NULL out), UNSUPPORTED_SHAPE, OUT_OF_MEMORY, CUDA.
  */
 TSMM_API tsmm_status tsmm_plan(int64_t m, int64_t n, int64_t k, tsmm_dtype dtype, tsmm_plan_t *out);
 

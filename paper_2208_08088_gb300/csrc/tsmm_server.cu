@@ -281,7 +281,13 @@ void tsmm_server_s::launch(double t) {
                 // failure may still be running, and the unit's memory stays in use
                 // until they are done.
                 if (cudaEventRecord(b.ev, u.st) != cudaSuccess) {
+                    // wait for what was enqueued, then clear the counters it may have
+                    // left part-way before the slices go back to the arena
                     cudaStreamSynchronize(u.st);
+                    cudaGetLastError();
+                    for (Req *q : b.reqs)
+                        if (q->ticket_bytes) cudaMemset(q->plan.tickets, 0, q->ticket_bytes);
+                    cudaDeviceSynchronize();
                     cudaGetLastError();
                     if (st == TSMM_OK) st = TSMM_ERR_CUDA;
                     finish(b, st, now_s());

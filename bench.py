@@ -497,7 +497,15 @@ def time_points(tsmm, torch, pts, tdt, steps, warmup, precision=0, world=1, rank
         lo, hi = slab[(m, n, k)]
         points.append({"m": m, "n": n, "k": k, "beta": beta, "rows": [lo, hi],
                        "avg_ms": sum(durs) / len(durs), "total_ms": sum(durs)})
-    launches = steps * sum(plans[(m, n, k)].launches_per_execute() for (m, n, k, _) in pts)
+    # regime (ii) in the native precision first copies, with a kernel of its own,
+    # an A that a tensor map cannot describe (column stride not a multiple of 16 bytes)
+    es = torch.empty((), dtype=tdt).element_size()
+
+    def per_execute(m, pl):
+        copy = precision == 0 and pl.info()["regime"] == 2 and ((m + lda_pad) * es) % 16 != 0
+        return pl.launches_per_execute() + (1 if copy else 0)
+
+    launches = steps * sum(per_execute(m, plans[(m, n, k)]) for (m, n, k, _) in pts)
     state = {"A": A, "packed": packed, "plans": plans, "C": C, "slab": slab, "pack_ms": pack_ms,
              "clocks": clocks}
     return points, elapsed_ms, launches, state

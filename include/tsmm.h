@@ -211,8 +211,8 @@ TSMM_API tsmm_status tsmm_plan_info(tsmm_plan_t plan, int *regime, int *np, int 
  * (i), and in regime (ii) copied first into an aligned scratch buffer taken
  * from the device's stream-ordered memory pool (cudaMallocAsync on `stream`,
  * released by cudaFreeAsync after the kernel; if that allocation fails, a
- * slower kernel with plain loads reads A directly).  Enqueues one to three
- * kernels on `stream` and returns.
+ * slower kernel with plain loads reads A directly).  Enqueues one kernel on
+ * `stream` (two when regime (ii) copies A first) and returns.
  */
 TSMM_API tsmm_status tsmm_execute(tsmm_plan_t plan, double alpha, const void *A_dev, int64_t lda,
                          tsmm_packed_b pb, double beta, void *C_dev, int64_t ldc,

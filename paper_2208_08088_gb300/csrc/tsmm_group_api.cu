@@ -65,8 +65,8 @@ tsmm_status validate(const tsmm_group_item &it) {
 }
 
 // 0: not groupable (its own tsmm_execute launch); 1: A described by a tensor
-// map; 2: A whose base or column stride is not 16-byte aligned (element copies
-// of heads and tails, bulk copies of the rest).
+// map; 2: A whose base or column stride is not 16-byte aligned (each column
+// moved by one bulk copy of the 16-byte-aligned span around its rows).
 int group_kind(const tsmm_group_item &it) {
     tsmm_plan_t p = it.plan;
     const size_t es = dtype_size(p->dtype);

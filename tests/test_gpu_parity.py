@@ -336,6 +336,37 @@ def test_rankk_wide_several_tiles_per_block(m, k, beta):
     assert_parity(C, A, B, C0 if beta != 0 else None, 1.5, beta, exact=True)
 
 
+@pytest.mark.parametrize("alpha", [1.0, -0.5])
+@pytest.mark.parametrize("k", [64, 128])
+@pytest.mark.parametrize("m", [1024, 1001])
+def test_rankk_beta_one_subnormals_exact(m, k, alpha):
+    """FP32, k > 32, beta = 1 (C = C0 + alpha*AB in one rounding: by a TMA
+    reduce-add of alpha*acc when C meets the TMA rules, m = 1024, and by the
+    plain epilogue's fma(1, C0, alpha*acc), m = 1001): subnormals are
+    neither read nor written as zero.  In the first half of the rows A is zero
+    and C keeps its subnormal C0; in the other half alpha*AB is alpha * 2^-126
+    (alpha = -0.5: itself subnormal) and C0 = s - alpha * 2^-126 with s a
+    subnormal, so C = s exactly."""
+    n = 320
+    rng = np.random.default_rng(11)
+    A = np.zeros((m, k), np.float32, order="F")
+    B = np.zeros((k, n), np.float32, order="F")
+    half = m // 2
+    A[half:, 3] = np.float32(2.0 ** -63)
+    B[3, :] = np.float32(2.0 ** -63)
+    tiny = 2.0 ** -149
+    s = rng.integers(-(2 ** 20), 2 ** 20, size=(m, n)).astype(np.float64) * tiny
+    C0 = s.copy()
+    C0[half:] -= alpha * 2.0 ** -126
+    C0 = np.asfortranarray(C0.astype(np.float32))
+    assert np.array_equal(C0.astype(np.float64), np.where(np.arange(m)[:, None] < half, s,
+                                                          s - alpha * 2.0 ** -126))  # exact
+    C, pl, _ = run(A, B, C0, alpha, 1.0)
+    assert pl.info()["regime"] == 2
+    np.testing.assert_array_equal(C, s.astype(np.float32))
+    assert_parity(C, A, B, C0, alpha, 1.0, exact=True)
+
+
 @pytest.mark.parametrize("k", [1, 8, 32])
 def test_rankk_f64_alpha_beta_one_integer_exact(k):
     """FP64 with alpha = beta = 1 and k within one chunk starts its

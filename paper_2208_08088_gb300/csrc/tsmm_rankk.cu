@@ -736,8 +736,10 @@ __global__ void __launch_bounds__(WideCfg<TMA_EPI, KC>::THREADS, WideCfg<TMA_EPI
     const int c0 = (warp >> 1) * 32 + ln * 4;  // local columns c0..c0+3 and c0+16..c0+19
     const float alpha = static_cast<float>(a.alpha);
     const float beta = static_cast<float>(a.beta);
+    const bool alpha1 = alpha == 1.0f;  // alpha*x == x exactly: no multiply
     float *C = static_cast<float *>(a.C);
-    int64_t g = 0;
+    int st = 0;       // ring slot of the next chunk
+    uint32_t ph = 0;  // and the parity of its phase
     int j = 0;
     bool ok = true;
     for (int64_t t = blockIdx.x; t < ntiles_total && ok; t += gridDim.x, ++j) {
@@ -746,19 +748,22 @@ __global__ void __launch_bounds__(WideCfg<TMA_EPI, KC>::THREADS, WideCfg<TMA_EPI
         const int64_t i0 = mt * W::BMT;
         WideAcc acc;
         acc.zero();
-        for (int c = 0; c < nchunks; ++c, ++g) {
-            const int st = (int)(g % W::STAGES);
-            if (!mbar_wait_bounded(&full[st], (uint32_t)((g / W::STAGES) & 1))) {
+        for (int c = 0; c < nchunks; ++c) {
+            if (!mbar_wait_bounded(&full[st], ph)) {
                 ok = false;
                 break;
             }
-            const int64_t kc = (int64_t)c * W::KC;
-            const int kcnt = (int)((a.k - kc < W::KC) ? a.k - kc : W::KC);
+            const int kc = c * W::KC;  // k <= kRankMaxK
+            const int kcnt = (int)a.k - kc < W::KC ? (int)a.k - kc : W::KC;
             const float *sA = sStage + st * W::STAGE_ELEMS;
             acc.chunk<W::KC>(sA, sA + W::A_CHUNK, kcnt, r0, c0);
             release_reads_to_async_copy();
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty[st]);
+            if (++st == W::STAGES) {
+                st = 0;
+                ph ^= 1u;
+            }
         }
         if (!ok) break;
         if constexpr (TMA_EPI) {
@@ -773,8 +778,13 @@ __global__ void __launch_bounds__(WideCfg<TMA_EPI, KC>::THREADS, WideCfg<TMA_EPI
                 for (int rg = 0; rg < 2; ++rg) {
                     float4 *p = reinterpret_cast<float4 *>(cbuf + cl * W::BMT + r0 + rg * 32);
                     const bool with_c0 = use_c0 && !add_c0;
-                    const float4 c0v = with_c0 ? *p : make_float4(0.f, 0.f, 0.f, 0.f);
-                    *p = axpby4(alpha, acc.rows(rg, cc), beta, c0v, with_c0);
+                    const float4 x = acc.rows(rg, cc);
+                    if (alpha1 && !with_c0) {
+                        *p = x;
+                    } else {
+                        const float4 c0v = with_c0 ? *p : make_float4(0.f, 0.f, 0.f, 0.f);
+                        *p = axpby4(alpha, x, beta, c0v, with_c0);
+                    }
                 }
             }
             // results in the buffer, visible to the tensor copy: the producer stores them

@@ -367,6 +367,30 @@ def test_rankk_beta_one_subnormals_exact(m, k, alpha):
     assert_parity(C, A, B, C0, alpha, 1.0, exact=True)
 
 
+@pytest.mark.parametrize("k", [16, 64])
+@pytest.mark.parametrize("m", [1024, 1001])
+def test_rankk_ieee_specials_propagate(m, k):
+    """FP32 regime (ii) with beta = 1 (k = 64: the TMA reduce-add into C when C
+    meets the TMA rules, m = 1024): infinities and NaNs in A and in C0 reach C as
+    the oracle has them, including inf + (-inf) = NaN between the product and C0."""
+    n = 300
+    A, B, C0 = gen(m, n, k, np.float32)
+    A, B, C0 = A.copy(order="F"), np.abs(B).astype(np.float32, order="F"), C0.copy(order="F")
+    A[5, 3] = np.inf
+    A[77, 10] = np.nan
+    A[300, :] = 0.0
+    A[300, 0] = np.inf        # row 300: +inf products (B >= 0, B[0] > 0 where checked)
+    B[0, :] = np.maximum(B[0, :], np.float32(0.25))
+    C0[300, 100] = -np.inf    # +inf + (-inf) = NaN
+    C0[300, 101] = np.inf     # +inf + inf = inf
+    C0[200, 17] = np.nan
+    C0[400, 250] = -np.inf
+    C, pl, _ = run(A, B, C0, 1.0, 1.0)
+    assert pl.info()["regime"] == 2
+    assert np.isnan(C[300, 100]) and C[300, 101] == np.inf and np.isnan(C[200, 17]) and C[400, 250] == -np.inf
+    assert_parity(C, A, B, C0, 1.0, 1.0)
+
+
 @pytest.mark.parametrize("k", [1, 8, 32])
 def test_rankk_f64_alpha_beta_one_integer_exact(k):
     """FP64 with alpha = beta = 1 and k within one chunk starts its

@@ -233,6 +233,22 @@ def test_ieee_special_values(dtype):
     assert np.all(np.isnan(Cref[2]))
 
 
+def test_subnormals_are_ordinary_values():
+    """FP32 subnormals (below 2^-126) are kept, not flushed: with a zero
+    product C = C0 exactly; a product of 2^-126 plus a C0 of -0.75 * 2^-126
+    gives the subnormal 2^-128; products 2^-138 + 2^-149 sum to a subnormal
+    exactly (values fixed by hand)."""
+    t = np.float32
+    A = F(np.array([[0.0, 0.0], [2.0 ** -63, 0.0], [2.0 ** -75, 2.0 ** -75]], dtype=t))
+    B = F(np.array([[2.0 ** -63, 1.0], [2.0 ** -74, 1.0]], dtype=t))
+    C0 = F(np.array([[3 * 2.0 ** -149, -(2.0 ** -140)], [-0.75 * 2.0 ** -126, 0.0], [0.0, 0.0]], dtype=t))
+    Cref, _ = oracle.tsmm(1.0, A, B, 1.0, C0)
+    C = oracle.round_to(Cref, t)
+    assert C[0, 0] == 3 * 2.0 ** -149 and C[0, 1] == -(2.0 ** -140)  # A = 0: C0 kept
+    assert C[1, 0] == 2.0 ** -128                                     # 2^-126 - 0.75 * 2^-126
+    assert C[2, 0] == 2.0 ** -138 + 2.0 ** -149                       # 2049 * 2^-149
+
+
 # ---------------------------------------------------------------- accuracy
 def _exact(A, B, alpha, beta, C0):
     m, k = A.shape
